@@ -1,0 +1,185 @@
+/* ccmg.h - C ABI of the GB300 fourth-order cut-cell multigrid Poisson solver.
+ *
+ * Problem (Sec. 1, eq. poissonEquation / poissonBoundaryCondition of arXiv
+ * 2410.05865): Lap phi = f in Omega, N phi = g on dOmega, with Omega = the unit
+ * box minus a union of axis-aligned ellipsoids, N = Dirichlet or Neumann.
+ * Unknowns and results are cell averages <phi>_i (Sec. 2.3); the data are the
+ * cell averages <f>_i, the face averages <g> on the box faces, and the patch
+ * averages <<g>>_i on the irregular boundary (Sec. 2.3-2.4).  The discrete
+ * system L phi = r := f - N g (Sec. 2.4) is solved by Alg. Multigrid with
+ * Alg. VCycle (Sec. 5.3): omega-Jacobi on phi1 (SMO-1) + LU-correction on phi2
+ * (SMO-2), volume-weighted restriction, piecewise-constant prolongation, and a
+ * direct bottom solve.
+ *
+ * Conventions
+ *  - A grid array of level m has n_m^3 doubles, index (i*n_m + j)*n_m + k for
+ *    the cell [i,i+1]x[j,j+1]x[k,k+1] h_m (k fastest); h_m = 2^m / n.
+ *    Entries of cells that are not unknowns (exterior, or absorbed by merging)
+ *    are ignored on input and written as 0 (results: the owner's value).
+ *  - "where": CC_HOST (0) for host pointers, CC_DEVICE (1) for device pointers
+ *    on the solver's device.  Device pointers must stay valid until the call's
+ *    work on the solver's stream has finished.
+ *  - The caller owns every buffer it passes; the library copies inputs and keeps
+ *    no caller pointer after a call returns.  A cc_solver is freed only by
+ *    cc_destroy.  Calls on one solver are not thread-safe; distinct solvers are
+ *    independent.
+ *  - Every call returns a cc_status and never aborts; cc_last_error gives a
+ *    message for the last failure on a solver.
+ */
+#ifndef CCMG_H
+#define CCMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_solver cc_solver;
+
+typedef enum {
+  CC_OK = 0,
+  CC_ERR_INVALID_ARG = 1,
+  CC_ERR_OOM = 2,
+  CC_ERR_CUDA = 3,
+  CC_ERR_PLG = 4,          /* no poised lattice on the finest level */
+  CC_ERR_SINGULAR = 5,     /* zero or tiny pivot in an LU factorisation */
+  CC_ERR_NOT_CONVERGED = 6,
+  CC_ERR_DIVERGED = 7,     /* non-finite residual */
+  CC_ERR_MERGE = 8,        /* cell merging could not make every cell theta-proper */
+  CC_ERR_TIMEOUT = 9
+} cc_status;
+
+enum { CC_DIRICHLET = 0, CC_NEUMANN = 1 };
+enum { CC_HOST = 0, CC_DEVICE = 1 };
+
+typedef struct {
+  double centre[3];
+  double semi[3]; /* semi-axes (> 0); a sphere has three equal ones */
+} cc_shape;
+
+typedef struct {
+  int n;                  /* cells per axis on the finest level (>= 16, even for coarsening) */
+  int nshapes;
+  const cc_shape* shapes; /* removed from the box [0,1]^3 */
+  int shape_bc;           /* CC_DIRICHLET or CC_NEUMANN on every shape */
+  int box_bc[6];          /* faces x-, x+, y-, y+, z-, z+ */
+} cc_geometry;
+
+typedef struct {
+  double omega;      /* Jacobi weight (0.5) */
+  int nu1, nu2;      /* smoothing steps before / after the coarse correction (3, 3) */
+  int max_iter;      /* I_max of Alg. Multigrid (200) */
+  double rel_tol;    /* epsilon of Alg. Multigrid, on ||s|| / ||r|| (1e-10) */
+  int min_coarse_n;  /* coarsening stops before n < min_coarse_n (16) */
+  int max_levels;    /* (16) */
+  int use_graph;     /* capture each V-cycle + outer update in a CUDA graph (1) */
+  int lu_leaf;       /* nested-dissection leaf size (64) */
+  int host_threads;  /* OpenMP threads for the setup (0 = default) */
+} cc_params;
+
+typedef struct {
+  int iters;              /* V-cycles performed */
+  int converged;
+  double rel_resid;       /* final ||s|| / ||r|| */
+  double resid_hist[256]; /* ||s|| / ||r|| before each V-cycle (first 256) */
+  double ms_solve;        /* wall time of the solve on the stream (CUDA events) */
+} cc_stats;
+
+typedef struct {
+  int n_levels;
+  int n[16];
+  int n_unknowns[16];
+  int n_phi2[16];
+  int lu_height[16];
+  long long lu_entries[16];   /* stored factor entries (LU-correction; bottom level: whole L^(M)) */
+  long long phi2_nnz[16];
+  int n_cut;                  /* cut cells on the finest level */
+  int n_patches;              /* merged cells with a boundary patch, finest level */
+  long long cut_nodes;        /* volume quadrature nodes of the cut cells */
+  long long patch_nodes;      /* surface quadrature nodes of the patches */
+  double ms_setup_host;
+  double ms_setup_device;
+} cc_info;
+
+/* Fills the defaults given above. */
+void cc_default_params(cc_params* p);
+
+/* Host setup (geometry, merging, split, PLG + WLS rows, coarsening, nested
+ * dissection + LU factors) and upload to `device`.  device < 0 sets up on the
+ * host only: the query calls work, every GPU call returns CC_ERR_INVALID_ARG.  Errors: CC_ERR_INVALID_ARG,
+ * CC_ERR_PLG, CC_ERR_MERGE, CC_ERR_SINGULAR, CC_ERR_OOM, CC_ERR_CUDA. */
+cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solver** out);
+void cc_destroy(cc_solver* s);
+const char* cc_status_str(cc_status st);
+/* Copies the last error message of s (NUL-terminated, truncated to len); with
+ * s == NULL, the message of the last failed cc_setup on the calling thread. */
+cc_status cc_last_error(const cc_solver* s, char* buf, int len);
+/* Runs the solver's work on this CUDA stream (a cudaStream_t; NULL = the
+ * library's own non-blocking stream).  Drops a captured graph. */
+cc_status cc_set_stream(cc_solver* s, void* stream);
+cc_status cc_sync(cc_solver* s);
+
+cc_status cc_query(const cc_solver* s, cc_info* info);
+
+/* Per-cell maps of a level (host arrays of n_m^3): kind 0 exterior / 1 full /
+ * 2 cut; typ 0 none / 1 phi1 / 2 phi2; owner (-1 empty); volume in units of
+ * h_m^3.  Any pointer may be NULL. */
+cc_status cc_cell_map(const cc_solver* s, int level, int8_t* kind, uint8_t* typ, int32_t* owner, double* vol);
+
+/* Quadrature of the finest level's cut cells, so that callers can form <f>_i
+ * and <<g>>_i: cells[n_cut] grid indices, ptr[n_cut+1] node ranges,
+ * xyz[3*cut_nodes], w[cut_nodes] (absolute coordinates; w sums to the cut
+ * volume).  Sizes from cc_query. */
+cc_status cc_cut_nodes(const cc_solver* s, int32_t* cells, int64_t* ptr, double* xyz, double* w);
+/* Patches in the order g_patch uses: owners[n_patches] (grid index of the
+ * merged owner), ptr[n_patches+1], xyz/w/normal (normal = outward of Omega). */
+cc_status cc_patch_nodes(const cc_solver* s, int32_t* owners, int64_t* ptr, double* xyz, double* w, double* normal);
+/* The phi2 rows of a level (host arrays): cells[n_phi2]; CSR ptr[n_phi2+1],
+ * cols[nnz] (grid indices), vals[nnz] (entries of L); boundary terms bptr,
+ * bpatch (patch number, finest level only), bcoef (coefficient of <<g>>). */
+cc_status cc_phi2_rows(const cc_solver* s, int level, int32_t* cells, int32_t* ptr, int32_t* cols, double* vals,
+                       int32_t* bptr, int32_t* bpatch, double* bcoef);
+
+/* r = f - N g on the finest level (Sec. 2.4).  f: grid array of cell averages
+ * over C_i ∩ Omega (cut cells: over the fluid part); g_box: 6 n^2 face
+ * averages (face (2d+side), then the two other cell indices in axis order;
+ * Dirichlet: <phi>, Neumann: <d phi/d n> with n outward); g_patch[n_patches]:
+ * <<g>> per patch (Dirichlet: <<phi>>, Neumann: <<d phi/d n>>). */
+cc_status cc_rhs(cc_solver* s, const double* f, const double* g_box, const double* g_patch, double* r, int where);
+
+/* Alg. Multigrid from the initial guess in phi (zero if all zeros), until
+ * ||s||/||r|| < rel_tol or max_iter V-cycles.  phi receives the result.
+ * Returns CC_ERR_NOT_CONVERGED (phi = last iterate) or CC_ERR_DIVERGED. */
+cc_status cc_solve(cc_solver* s, const double* f, const double* g_box, const double* g_patch, double* phi,
+                   int where, cc_stats* stats);
+/* The same iteration for an already assembled r (grid array). */
+cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_stats* stats);
+
+/* ---- hot-path steps, device pointers, grid arrays of `level`, FP64 ------- */
+/* out = s - L phi on phi1 rows (and on phi2 rows if phi2_rows != 0, else 0). */
+cc_status cc_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* out, int phi2_rows);
+/* SMO-1: phi_out = phi_in + omega D^{-1} (rhs - L phi_in) on phi1, copy elsewhere. */
+cc_status cc_jacobi(cc_solver* s, int level, const double* phi_in, const double* rhs, double* phi_out);
+/* SMO-2 in place: phi2 <- L22^{-1} (rhs2 - L21 phi1). */
+cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* rhs);
+/* Restrict: coarse[I] = 2^-3 sum of (rhs - L phi) over the phi1 children of I. */
+cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* coarse);
+/* Prolong: phi1 cells of `level` += coarse value of the parent. */
+cc_status cc_prolong_add(cc_solver* s, int level, const double* coarse, double* phi);
+/* Bottom solver: phi = L^(M)^{-1} rhs on the coarsest level. */
+cc_status cc_bottom_solve(cc_solver* s, const double* rhs, double* phi);
+/* e = VCycle(s) on level 0 (zero initial correction). */
+cc_status cc_vcycle(cc_solver* s, const double* rhs, double* e);
+
+/* Per-kernel timing of the next solves (CUDA events around every launch,
+ * graphs off): enable != 0 starts and clears the counters. */
+cc_status cc_profile(cc_solver* s, int enable);
+/* name of kernel class k (NULL past the end), its launches and total ms */
+const char* cc_profile_entry(const cc_solver* s, int k, long long* launches, double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCMG_H */

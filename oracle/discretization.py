@@ -16,8 +16,11 @@ Paper passages followed
   least-squares fit of degree 4 (Sec. 2.3); the row is <Lap p>_i.
 
 Readings where the paper is silent (each listed in the design doc):
-* theta = 0.1; a common face must have positive fluid area; ties in the
-  largest common face go to the lowest linear index; MAP-3 for all small cells
+* theta = 0.02 (at 0.1 the concave creases of overlapping ellipsoids lose so
+  many cells to merging that no poised lattice exists); a common face must
+  have positive fluid area; common faces
+  within 1e-12 h^2 of the largest count as ties, which go to the lowest
+  linear index; MAP-3 for all small cells
   first (targets: theta-proper cells), then the BFS of Alg. CellMerging for any
   cell still below theta.  Cells are treated as single-component.
 * phi1 needs every in-box cell of {i, i±e^d, i±2e^d} to be a full cell that
@@ -38,7 +41,8 @@ import scipy.sparse as sp
 
 from .geometry import GL_W, GL_X, MONO, MONO3, MONO_INDEX, Q, CellGeometry
 
-THETA = 0.1
+THETA = 0.02
+AREA_TIE = 1e-12   # common-face areas (units h^2) this close count as equal
 RANK_TOL = 1e-10   # min |R_kk| / max |R_kk| of the weighted LS matrix
 
 DIRICHLET = 0
@@ -224,15 +228,11 @@ class Level:
         small = [int(i) for i in np.nonzero((self.kind == 2) & (self.vol < theta))[0]]
         # MAP-3: absorb into the theta-proper neighbour with the largest common face
         for i in small:
-            best, best_a = -1, 0.0
-            for j in self.neighbours(i):
-                if not proper[j]:
-                    continue
-                a = self._area(i, j)
-                if a > best_a or (a == best_a and a > 0.0 and j < best):
-                    best, best_a = j, a
-            if best >= 0:
-                owner[i] = best
+            cand = [(j, self._area(i, j)) for j in self.neighbours(i) if proper[j]]
+            cand = [(j, a) for j, a in cand if a > 0.0]
+            if cand:
+                amax = max(a for _, a in cand)
+                owner[i] = min(j for j, a in cand if a >= amax - AREA_TIE)
         # BFS for cells still below theta
         gvol = {}
         for i in range(N):

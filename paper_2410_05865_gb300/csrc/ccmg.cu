@@ -1,0 +1,1346 @@
+// GB300 (sm_103a) kernels of the cut-cell multigrid V-cycle and the C ABI.
+//
+// Data layout in HBM (per level m, n = n_m):
+//   grid arrays   n^3 doubles, index (i*n + j)*n + k (k fastest): phi, s, e, tmp
+//   typ           n^3 bytes: 0 none, 1 phi1, 2 phi2
+//   phi2 rows     CSR over the phi2 cells (grid-index columns), FP64
+//   LU factors    per supernode: inv(L_ss), inv(U_ss), L_{struct,s}, U_{s,struct}
+//                 (row-major FP64), plus row tasks grouped by tree height
+// The regular 13-point rows (eq. regularLaplaceDiscretization, box ghosts
+// eliminated) are not stored: each kernel evaluates them from a per-level table
+// of 1-D rows by position class {0, 1, interior, n-2, n-1}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ccmg.h"
+#include "setup.hpp"
+
+using namespace ccmg;
+
+namespace {
+
+// ------------------------------------------------------------------ kernels
+struct StencilP {
+  int n;
+  double inv12h2;
+  double c[3][5][7];  // per axis, position class, offsets -3..3 (times 12 h^2)
+  double g[3][5];     // coefficient of the nearer wall's <g> (times 12 h^2)
+};
+
+__device__ __forceinline__ int pos_class(int p, int n) {
+  return p == 0 ? 0 : (p == 1 ? 1 : (p == n - 2 ? 3 : (p == n - 1 ? 4 : 2)));
+}
+
+// (L phi)_i for a phi1 cell and the diagonal of its row.
+__device__ __forceinline__ double apply_regular(const double* __restrict__ phi, int i, int j, int k,
+                                                const StencilP& P, double* diag) {
+  const int n = P.n;
+  const long long nn = (long long)n * n;
+  const long long idx = (long long)i * nn + (long long)j * n + k;
+  const int ci = pos_class(i, n), cj = pos_class(j, n), ck = pos_class(k, n);
+  if (ci == 2 && cj == 2 && ck == 2) {
+    const double c0 = phi[idx];
+    double s1 = phi[idx + nn] + phi[idx - nn] + phi[idx + n] + phi[idx - n] + phi[idx + 1] + phi[idx - 1];
+    double s2 = phi[idx + 2 * nn] + phi[idx - 2 * nn] + phi[idx + 2 * n] + phi[idx - 2 * n] + phi[idx + 2] +
+                phi[idx - 2];
+    *diag = -90.0 * P.inv12h2;
+    return (16.0 * s1 - s2 - 90.0 * c0) * P.inv12h2;
+  }
+  const int cls[3] = {ci, cj, ck};
+  const long long stride[3] = {nn, (long long)n, 1};
+  double acc = 0.0, dg = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double* c = P.c[d][cls[d]];
+#pragma unroll
+    for (int o = -3; o <= 3; ++o) {
+      const double w = c[o + 3];
+      if (w != 0.0) acc += w * phi[idx + o * stride[d]];
+    }
+    dg += c[3];
+  }
+  *diag = dg * P.inv12h2;
+  return acc * P.inv12h2;
+}
+
+__global__ void k_jacobi(const double* __restrict__ phi_in, const double* __restrict__ s,
+                         double* __restrict__ phi_out, const uint8_t* __restrict__ typ, StencilP P, double omega) {
+  const int n = P.n;
+  const long long N = (long long)n * n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double v = phi_in[idx];
+    if (typ[idx] == 1) {
+      const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
+      double dg;
+      const double lphi = apply_regular(phi_in, i, j, k, P, &dg);
+      phi_out[idx] = v + omega * (s[idx] - lphi) / dg;
+    } else {
+      phi_out[idx] = v;
+    }
+  }
+}
+
+__global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
+                         const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
+  const int n = P.n;
+  const long long N = (long long)n * n * n;
+  double acc = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    if (typ[idx] == 1) {
+      const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
+      double dg;
+      r = s[idx] - apply_regular(phi, i, j, k, P, &dg);
+    }
+    out[idx] = r;
+    acc += r * r;
+  }
+  if (norm2) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(norm2, acc);
+  }
+}
+
+// s - L phi on the phi2 rows (PLG rows), optionally accumulating ||.||^2
+__global__ void k_resid2(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
+                         int n2, const int* __restrict__ cell, const int* __restrict__ ptr,
+                         const int* __restrict__ col, const double* __restrict__ val, double* __restrict__ norm2) {
+  double acc = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n2; r += gridDim.x * blockDim.x) {
+    double v = s[cell[r]];
+    for (int p = ptr[r]; p < ptr[r + 1]; ++p) v -= val[p] * phi[col[p]];
+    out[cell[r]] = v;
+    acc += v * v;
+  }
+  if (norm2) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(norm2, acc);
+  }
+}
+
+// coarse[I] = 2^-3 sum over the phi1 children of (s - L phi)
+__global__ void k_restrict(const double* __restrict__ phi, const double* __restrict__ s,
+                           double* __restrict__ coarse, const uint8_t* __restrict__ typ, StencilP P) {
+  const int n = P.n, nc = n / 2;
+  const long long Nc = (long long)nc * nc * nc;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(I / ((long long)nc * nc)), b = (int)((I / nc) % nc), c = (int)(I % nc);
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = 2 * a + (t >> 2), j = 2 * b + ((t >> 1) & 1), k = 2 * c + (t & 1);
+      const long long idx = ((long long)i * n + j) * n + k;
+      if (typ[idx] == 1) {
+        double dg;
+        acc += s[idx] - apply_regular(phi, i, j, k, P, &dg);
+      }
+    }
+    coarse[I] = 0.125 * acc;
+  }
+}
+
+__global__ void k_prolong(const double* __restrict__ coarse, double* __restrict__ phi,
+                          const uint8_t* __restrict__ typ, int n) {
+  const long long N = (long long)n * n * n;
+  const int nc = n / 2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (typ[idx] != 1) continue;
+    const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
+    phi[idx] += coarse[((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1)];
+  }
+}
+
+// b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
+__global__ void k_lu_rhs(double* __restrict__ b, int np, const int* __restrict__ cell, const int* __restrict__ ptr,
+                         const int* __restrict__ col, const double* __restrict__ val,
+                         const double* __restrict__ s, const double* __restrict__ phi) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    double v = s[cell[p]];
+    for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * phi[col[q]];
+    b[p] = v;
+  }
+}
+
+__global__ void k_scatter(const double* __restrict__ x, int np, const int* __restrict__ cell, double* __restrict__ phi) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) phi[cell[p]] = x[p];
+}
+
+struct Task {
+  long long moff;  // first value of the matrix row
+  int ncols;
+  int xoff;        // first input position (or first gather index)
+  int out;         // output position
+  int pad;
+};
+
+enum { T_F1 = 0, T_F2 = 1, T_B1 = 2, T_B2 = 3 };
+
+// One warp per matrix row: dot product of a dense row with a vector segment.
+template <int MODE>
+__global__ void k_tasks(const Task* __restrict__ tasks, int ntasks, const double* __restrict__ vals,
+                        const double* __restrict__ xin, const int* __restrict__ gidx, const double* __restrict__ yin,
+                        double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < ntasks; t += nwarps) {
+    const Task tk = tasks[t];
+    const double* __restrict__ row = vals + tk.moff;
+    double acc = 0.0;
+    if (MODE == T_B1) {
+      const int* __restrict__ g = gidx + tk.xoff;
+      for (int j = lane; j < tk.ncols; j += 32) acc += row[j] * xin[g[j]];
+    } else {
+      const double* __restrict__ x = xin + tk.xoff;
+      for (int j = lane; j < tk.ncols; j += 32) acc += row[j] * x[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      if (MODE == T_F1 || MODE == T_B2)
+        out[tk.out] = acc;
+      else if (MODE == T_F2)
+        atomicAdd(out + tk.out, -acc);
+      else
+        out[tk.out] = yin[tk.out] - acc;
+    }
+  }
+}
+
+__global__ void k_axpy(double* __restrict__ phi, const double* __restrict__ e, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    phi[i] += e[i];
+}
+
+__global__ void k_mask(double* __restrict__ v, const uint8_t* __restrict__ typ, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    if (typ[i] == 0) v[i] = 0.0;
+}
+
+__global__ void k_norm2(const double* __restrict__ v, long long N, double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    acc += v[i] * v[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// r = f for unknowns (0 elsewhere), minus the ghost terms of phi1 rows next to the box.
+__global__ void k_rhs_base(const double* __restrict__ f, const double* __restrict__ gbox, double* __restrict__ r,
+                           const uint8_t* __restrict__ typ, StencilP P) {
+  const int n = P.n;
+  const long long N = (long long)n * n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = typ[idx];
+    double v = t ? f[idx] : 0.0;
+    if (t == 1) {
+      const int c[3] = {(int)(idx / ((long long)n * n)), (int)((idx / n) % n), (int)(idx % n)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int cl = pos_class(c[d], n);
+        if (cl == 2) continue;
+        const int side = cl >= 3 ? 1 : 0;
+        const int t0 = d == 0 ? c[1] : c[0];
+        const int t1 = d == 2 ? c[1] : c[2];
+        const double gv = gbox[((long long)(2 * d + side) * n + t0) * n + t1];
+        v -= P.g[d][cl] * P.inv12h2 * gv;
+      }
+    }
+    r[idx] = v;
+  }
+}
+
+// owners of merged cells: r[o] = sum_p w_p f[p]   (volume-weighted mean, Sec. 4.2)
+__global__ void k_merge_f(int ng, const int* __restrict__ owner, const int* __restrict__ ptr,
+                          const int* __restrict__ part, const double* __restrict__ w, const double* __restrict__ f,
+                          double* __restrict__ r) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int q = ptr[g]; q < ptr[g + 1]; ++q) v += w[q] * f[part[q]];
+    r[owner[g]] = v;
+  }
+}
+
+// phi2 rows: r -= sum_b coef_b <<g>>_b
+__global__ void k_patch_terms(int n2, const int* __restrict__ cell, const int* __restrict__ bptr,
+                              const int* __restrict__ bpatch, const double* __restrict__ bcoef,
+                              const double* __restrict__ gpatch, double* __restrict__ r) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int p = bptr[q]; p < bptr[q + 1]; ++p) v += bcoef[p] * gpatch[bpatch[p]];
+    r[cell[q]] -= v;
+  }
+}
+
+// absorbed cells report their owner's value
+__global__ void k_absorbed(double* __restrict__ phi, int na, const int* __restrict__ cell, const int* __restrict__ own) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < na; q += gridDim.x * blockDim.x) phi[cell[q]] = phi[own[q]];
+}
+
+// ------------------------------------------------------------ host structs
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct DevLU {
+  int np = 0;       // dimension
+  int height = -1;
+  double* vals = nullptr;
+  int* structs = nullptr;
+  Task* tasks = nullptr;
+  std::vector<long long> toff[4];  // per phase: offsets by height (height+2)
+  long long ntasks[4] = {0, 0, 0, 0};
+  double *b = nullptr, *y = nullptr, *t = nullptr, *x = nullptr;
+  int* cell = nullptr;  // ND position -> grid index
+  int *rptr = nullptr, *rcol = nullptr;
+  double* rval = nullptr;
+  long long entries = 0;
+  long long task_bytes[4] = {0, 0, 0, 0};  // algorithmic bytes per solve phase (matrix + vectors)
+};
+
+struct DevLevel {
+  int n = 0;
+  long long N = 0;
+  StencilP P;
+  uint8_t* typ = nullptr;
+  int n2 = 0;
+  int *p2_cell = nullptr, *p2_ptr = nullptr, *p2_col = nullptr;
+  double* p2_val = nullptr;
+  long long p2_nnz = 0;
+  DevLU lu;
+  double *s = nullptr, *e = nullptr, *tmp = nullptr;
+};
+
+enum Prof {
+  P_JACOBI,
+  P_RESID1,
+  P_RESID2,
+  P_RESTRICT,
+  P_PROLONG,
+  P_LURHS,
+  P_F1,
+  P_F2,
+  P_B1,
+  P_B2,
+  P_SCATTER,
+  P_AXPY,
+  P_NORM,
+  P_RHS,
+  P_COUNT
+};
+const char* kProfNames[P_COUNT] = {"jacobi",      "resid_phi1", "resid_phi2", "restrict", "prolong",
+                                   "lu_rhs",      "trsv_fwd_diag", "trsv_fwd_update", "trsv_bwd_update",
+                                   "trsv_bwd_diag", "lu_scatter", "axpy", "norm", "rhs"};
+
+}  // namespace
+
+struct cc_solver {
+  int device = 0;
+  bool host_only = false;
+  cc_params prm;
+  std::vector<Level> host;
+  std::vector<DevLevel> lev;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  int nsm = 148;
+  // finest level extras
+  double *r = nullptr, *phi = nullptr, *s0 = nullptr, *f = nullptr, *gbox = nullptr, *gpatch = nullptr;
+  double* norm = nullptr;   // device scalar
+  double* hnorm = nullptr;  // pinned host scalar
+  int ngroups = 0;
+  int *g_owner = nullptr, *g_ptr = nullptr, *g_part = nullptr;
+  double* g_w = nullptr;
+  int nabs = 0;
+  int *a_cell = nullptr, *a_own = nullptr;
+  int n2_0 = 0;
+  int *b_ptr = nullptr, *b_patch = nullptr;
+  double* b_coef = nullptr;
+  std::vector<int> patch_owner;  // patch order
+  cc_info info;
+  // graphs
+  cudaGraphExec_t cycle_exec = nullptr;
+  // profiling
+  bool prof = false;
+  long long prof_launch[P_COUNT];
+  double prof_ms[P_COUNT];
+  double prof_bytes[P_COUNT];
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      S->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return e_ == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA;          \
+    }                                                                             \
+  } while (0)
+
+template <class T>
+cc_status dalloc(cc_solver* S, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  S->allocs.push_back((void*)*p);
+  return CC_OK;
+}
+
+template <class T>
+cc_status dupload(cc_solver* S, T** p, const std::vector<T>& v) {
+  cc_status st = dalloc(S, p, v.size());
+  if (st) return st;
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return CC_OK;
+}
+
+int grid_for(const cc_solver* S, long long work, int block) {
+  long long b = (work + block - 1) / block;
+  long long cap = (long long)S->nsm * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// profiling helpers: events around one launch
+struct ProfScope {
+  cc_solver* S;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(cc_solver* s, int c, double by) : S(s), cls(c), bytes(by) {
+    if (S->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, S->stream);
+    }
+  }
+  ~ProfScope() {
+    if (S->prof) {
+      cudaEventRecord(b, S->stream);
+      S->pending.push_back({cls, {a, b}});
+      S->prof_launch[cls] += 1;
+      S->prof_bytes[cls] += bytes;
+    }
+  }
+};
+
+void prof_flush(cc_solver* S) {
+  if (S->pending.empty()) return;
+  cudaStreamSynchronize(S->stream);
+  for (auto& pe : S->pending) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+    S->prof_ms[pe.first] += ms;
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  S->pending.clear();
+}
+
+StencilP make_stencil(const Level& L) {
+  StencilP P;
+  P.n = L.n;
+  P.inv12h2 = 1.0 / (12.0 * L.h * L.h);
+  for (int d = 0; d < 3; ++d) {
+    Rows1D r = regular_rows_1d(L.box_bc[2 * d], L.box_bc[2 * d + 1], L.h);
+    for (int c = 0; c < 5; ++c) {
+      for (int o = 0; o < 7; ++o) P.c[d][c][o] = r.c[c][o];
+      P.g[d][c] = r.g[c];
+    }
+  }
+  return P;
+}
+
+// CSR of the whole level operator over unknowns (for the bottom level)
+void full_operator(const Level& L, const StencilP& P, std::vector<int>& uid, std::vector<int>& cells,
+                   std::vector<int>& ptr, std::vector<int>& col, std::vector<double>& val, std::vector<int>& xyz) {
+  const int n = L.n;
+  const long long N = (long long)n * n * n;
+  uid.assign(N, -1);
+  cells.clear();
+  for (long long i = 0; i < N; ++i)
+    if (L.typ[i]) {
+      uid[i] = (int)cells.size();
+      cells.push_back((int)i);
+    }
+  std::map<int, int> p2row;
+  for (size_t r = 0; r < L.p2_cell.size(); ++r) p2row[L.p2_cell[r]] = (int)r;
+  ptr.assign(1, 0);
+  col.clear();
+  val.clear();
+  xyz.clear();
+  for (int c : cells) {
+    int ijk[3] = {c / (n * n), (c / n) % n, c % n};
+    xyz.insert(xyz.end(), ijk, ijk + 3);
+    std::map<int, double> row;
+    if (L.typ[c] == 1) {
+      const long long stride[3] = {(long long)n * n, n, 1};
+      for (int d = 0; d < 3; ++d) {
+        int p = ijk[d];
+        int cl = p == 0 ? 0 : (p == 1 ? 1 : (p == n - 2 ? 3 : (p == n - 1 ? 4 : 2)));
+        for (int o = -3; o <= 3; ++o) {
+          double w = P.c[d][cl][o + 3];
+          if (w != 0.0) row[(int)(c + o * stride[d])] += w * P.inv12h2;
+        }
+      }
+    } else {
+      int r = p2row[c];
+      for (int q = L.p2_ptr[r]; q < L.p2_ptr[r + 1]; ++q) row[L.p2_col[q]] += L.p2_val[q];
+    }
+    for (auto& kv : row) {
+      col.push_back(uid[kv.first]);
+      val.push_back(kv.second);
+    }
+    ptr.push_back((int)col.size());
+  }
+}
+
+cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<int>& pos_cell,
+                    const std::vector<int>& rptr, const std::vector<int>& rcol, const std::vector<double>& rval) {
+  D.np = F.n;
+  D.height = F.height;
+  D.entries = F.nnz_factor;
+  cc_status st;
+  if ((st = dupload(S, &D.vals, F.vals))) return st;
+  if ((st = dupload(S, &D.structs, F.structs))) return st;
+  std::vector<Task> all;
+  for (int ph = 0; ph < 4; ++ph) D.toff[ph].assign(F.height + 2, 0);
+  std::vector<Task> per[4];
+  std::vector<std::vector<Task>> byh[4];
+  for (int ph = 0; ph < 4; ++ph) byh[ph].assign(F.height + 1, {});
+  for (int s = 0; s < F.nsuper; ++s) {
+    const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+    const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+    const int hgt = F.sn_height[s];
+    for (int t = 0; t < k; ++t) {
+      // F1: y = inv(L_ss) b_s, lower triangle only (cols 0..t)
+      byh[T_F1][hgt].push_back({F.off_linv[s] + (long long)t * k, t + 1, f0, f0 + t, 0});
+      // B2: x = inv(U_ss) t_s, upper triangle (cols t..k-1)
+      byh[T_B2][hgt].push_back({F.off_uinv[s] + (long long)t * k + t, k - t, f0 + t, f0 + t, 0});
+      if (m > 0) byh[T_B1][hgt].push_back({F.off_u12[s] + (long long)t * m, m, (int)F.sn_struct[s], f0 + t, 0});
+      else byh[T_B1][hgt].push_back({0, 0, 0, f0 + t, 0});
+    }
+    for (int a = 0; a < m; ++a)
+      byh[T_F2][hgt].push_back({F.off_l21[s] + (long long)a * k, k, f0, F.structs[F.sn_struct[s] + a], 0});
+  }
+  for (int ph = 0; ph < 4; ++ph) {
+    long long bytes = 0;
+    for (int h = 0; h <= F.height; ++h) {
+      D.toff[ph][h] = (long long)all.size();
+      for (const Task& t : byh[ph][h]) {
+        all.push_back(t);
+        bytes += (long long)t.ncols * 8 * (ph == T_B1 ? 2 : 1) + 16;
+      }
+    }
+    D.toff[ph][F.height + 1] = (long long)all.size();
+    D.ntasks[ph] = D.toff[ph][F.height + 1] - D.toff[ph][0];
+    D.task_bytes[ph] = bytes;
+  }
+  if ((st = dupload(S, &D.tasks, all))) return st;
+  if ((st = dalloc(S, &D.b, F.n))) return st;
+  if ((st = dalloc(S, &D.y, F.n))) return st;
+  if ((st = dalloc(S, &D.t, F.n))) return st;
+  if ((st = dalloc(S, &D.x, F.n))) return st;
+  std::vector<int> cellv(F.n);
+  for (int p = 0; p < F.n; ++p) cellv[p] = pos_cell[F.perm[p]];
+  if ((st = dupload(S, &D.cell, cellv))) return st;
+  // RHS rows in ND order
+  std::vector<int> rp(1, 0), rc;
+  std::vector<double> rv;
+  for (int p = 0; p < F.n; ++p) {
+    int r = F.perm[p];
+    for (int q = rptr[r]; q < rptr[r + 1]; ++q) {
+      rc.push_back(rcol[q]);
+      rv.push_back(rval[q]);
+    }
+    rp.push_back((int)rc.size());
+  }
+  if ((st = dupload(S, &D.rptr, rp))) return st;
+  if ((st = dupload(S, &D.rcol, rc))) return st;
+  if ((st = dupload(S, &D.rval, rv))) return st;
+  return CC_OK;
+}
+
+// --------------------------------------------------------------- launches
+void launch_tasks(cc_solver* S, DevLU& D, int ph, int h) {
+  long long a = D.toff[ph][h], b = D.toff[ph][h + 1];
+  int nt = (int)(b - a);
+  if (nt <= 0) return;
+  const int block = 256;
+  int grid = grid_for(S, (long long)nt * 32, block);
+  const Task* T = D.tasks + a;
+  static const int cls[4] = {P_F1, P_F2, P_B1, P_B2};
+  ProfScope ps(S, cls[ph], 0.0);
+  switch (ph) {
+    case T_F1: k_tasks<T_F1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.b, nullptr, nullptr, D.y); break;
+    case T_F2: k_tasks<T_F2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.y, nullptr, nullptr, D.b); break;
+    case T_B1: k_tasks<T_B1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.x, D.structs, D.y, D.t); break;
+    case T_B2: k_tasks<T_B2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.t, nullptr, nullptr, D.x); break;
+  }
+}
+
+// phi[cells] = A^{-1} (s[cells] - R phi) with the stored factors
+void lu_solve(cc_solver* S, DevLU& D, const double* s, double* phi) {
+  if (D.np == 0) return;
+  const int block = 256;
+  {
+    ProfScope ps(S, P_LURHS, 0.0);
+    k_lu_rhs<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.np, D.cell, D.rptr, D.rcol, D.rval, s, phi);
+  }
+  for (int h = 0; h <= D.height; ++h) {
+    launch_tasks(S, D, T_F1, h);
+    launch_tasks(S, D, T_F2, h);
+  }
+  for (int h = D.height; h >= 0; --h) {
+    launch_tasks(S, D, T_B1, h);
+    launch_tasks(S, D, T_B2, h);
+  }
+  ProfScope ps(S, P_SCATTER, 0.0);
+  k_scatter<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
+}
+
+void jacobi(cc_solver* S, DevLevel& L, const double* in, const double* s, double* out) {
+  const int block = 256;
+  ProfScope ps(S, P_JACOBI, 25.0 * L.N);
+  k_jacobi<<<grid_for(S, L.N, block), block, 0, S->stream>>>(in, s, out, L.typ, L.P, S->prm.omega);
+}
+
+void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {
+  const int block = 256;
+  {
+    ProfScope ps(S, P_RESID1, 25.0 * L.N);
+    k_resid1<<<grid_for(S, L.N, block), block, 0, S->stream>>>(phi, s, out, L.typ, L.P, norm2);
+  }
+  if (phi2 && L.n2 > 0) {
+    ProfScope ps(S, P_RESID2, 12.0 * L.p2_nnz);
+    k_resid2<<<grid_for(S, L.n2, block), block, 0, S->stream>>>(phi, s, out, L.n2, L.p2_cell, L.p2_ptr, L.p2_col,
+                                                                 L.p2_val, norm2);
+  }
+}
+
+void restrict_resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* coarse) {
+  const int block = 256;
+  ProfScope ps(S, P_RESTRICT, 17.0 * L.N);
+  k_restrict<<<grid_for(S, L.N / 8, block), block, 0, S->stream>>>(phi, s, coarse, L.typ, L.P);
+}
+
+void prolong(cc_solver* S, DevLevel& L, const double* coarse, double* phi) {
+  const int block = 256;
+  ProfScope ps(S, P_PROLONG, 17.125 * L.N);
+  k_prolong<<<grid_for(S, L.N, block), block, 0, S->stream>>>(coarse, phi, L.typ, L.n);
+}
+
+void vcycle_rec(cc_solver* S, int m, const double* s, double* e) {
+  DevLevel& L = S->lev[m];
+  const int M = (int)S->lev.size() - 1;
+  cudaMemsetAsync(e, 0, L.N * sizeof(double), S->stream);
+  if (m == M) {
+    lu_solve(S, L.lu, s, e);
+    return;
+  }
+  double* cur = e;
+  double* oth = L.tmp;
+  for (int it = 0; it < S->prm.nu1; ++it) {
+    jacobi(S, L, cur, s, oth);
+    std::swap(cur, oth);
+    lu_solve(S, L.lu, s, cur);
+  }
+  DevLevel& C = S->lev[m + 1];
+  restrict_resid(S, L, cur, s, C.s);
+  vcycle_rec(S, m + 1, C.s, C.e);
+  prolong(S, L, C.e, cur);
+  for (int it = 0; it < S->prm.nu2; ++it) {
+    jacobi(S, L, cur, s, oth);
+    std::swap(cur, oth);
+    lu_solve(S, L.lu, s, cur);
+  }
+  if (cur != e) cudaMemcpyAsync(e, cur, L.N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream);
+}
+
+// s0 = r - L phi (all rows) and ||s0||^2 into S->norm
+void outer_residual(cc_solver* S) {
+  DevLevel& L = S->lev[0];
+  cudaMemsetAsync(S->norm, 0, sizeof(double), S->stream);
+  resid(S, L, S->phi, S->r, S->s0, true, S->norm);
+  cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+}
+
+void one_cycle(cc_solver* S) {
+  DevLevel& L = S->lev[0];
+  vcycle_rec(S, 0, S->s0, L.e);
+  {
+    ProfScope ps(S, P_AXPY, 24.0 * L.N);
+    k_axpy<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.e, L.N);
+  }
+  outer_residual(S);
+}
+
+// Patch list (merged owners with a boundary patch, increasing grid index) and
+// node counts of the finest level; returns grid -> patch number (-1 = none).
+std::vector<int> finish_host_info(cc_solver* S) {
+  const Level& L0 = S->host[0];
+  std::vector<int> patch_of(L0.typ.size(), -1);
+  S->patch_owner.clear();
+  for (size_t gi = 0; gi < L0.groups.size(); ++gi)
+    if (L0.msrf[gi][0] > 0.0) patch_of[L0.groups[gi][0]] = 0;
+  for (size_t i = 0; i < patch_of.size(); ++i)
+    if (patch_of[i] == 0) {
+      patch_of[i] = (int)S->patch_owner.size();
+      S->patch_owner.push_back((int)i);
+    }
+  S->info.n_patches = (int)S->patch_owner.size();
+  S->info.n_cut = (int)L0.geo.cut_cells.size();
+  long long cn = 0, pn = 0;
+  for (const auto& nd : L0.geo.nodes) {
+    cn += (long long)nd.vw.size();
+    pn += (long long)nd.sw.size();
+  }
+  S->info.cut_nodes = cn;
+  S->info.patch_nodes = pn;
+  return patch_of;
+}
+
+cc_status fail(cc_solver* S, cc_status st, const std::string& msg) {
+  S->err = msg;
+  return st;
+}
+
+cc_status check_level(cc_solver* S, int level) {
+  if (level < 0 || level >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "level out of range");
+  return CC_OK;
+}
+
+void drop_graph(cc_solver* S) {
+  if (S->cycle_exec) {
+    cudaGraphExecDestroy(S->cycle_exec);
+    S->cycle_exec = nullptr;
+  }
+}
+
+cc_status build_rhs(cc_solver* S, const double* f, const double* gbox, const double* gpatch, int where) {
+  DevLevel& L = S->lev[0];
+  const int n = L.n;
+  const size_t Nb = L.N * sizeof(double);
+  cudaMemcpyKind k = where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!f || !gbox) return fail(S, CC_ERR_INVALID_ARG, "f and g_box are required");
+  if (S->info.n_patches > 0 && !gpatch) return fail(S, CC_ERR_INVALID_ARG, "g_patch is required");
+  CK(cudaMemcpyAsync(S->f, f, Nb, k, S->stream));
+  CK(cudaMemcpyAsync(S->gbox, gbox, (size_t)6 * n * n * sizeof(double), k, S->stream));
+  if (S->info.n_patches > 0)
+    CK(cudaMemcpyAsync(S->gpatch, gpatch, (size_t)S->info.n_patches * sizeof(double), k, S->stream));
+  ProfScope ps(S, P_RHS, 0.0);
+  k_rhs_base<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->f, S->gbox, S->r, L.typ, L.P);
+  if (S->ngroups)
+    k_merge_f<<<grid_for(S, S->ngroups, 128), 128, 0, S->stream>>>(S->ngroups, S->g_owner, S->g_ptr, S->g_part,
+                                                                    S->g_w, S->f, S->r);
+  if (S->n2_0)
+    k_patch_terms<<<grid_for(S, S->n2_0, 128), 128, 0, S->stream>>>(S->n2_0, L.p2_cell, S->b_ptr, S->b_patch,
+                                                                     S->b_coef, S->gpatch, S->r);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
+  DevLevel& L = S->lev[0];
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, S->stream));
+  // ||r||
+  CK(cudaMemsetAsync(S->norm, 0, sizeof(double), S->stream));
+  k_norm2<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->r, L.N, S->norm);
+  CK(cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  const double rn = std::sqrt(*S->hnorm);
+  outer_residual(S);
+  CK(cudaStreamSynchronize(S->stream));
+  cc_status result = CC_ERR_NOT_CONVERGED;
+  int it = 0;
+  double rel = 0;
+  const bool use_graph = S->prm.use_graph && !S->prof;
+  for (;; ++it) {
+    if (S->prof) prof_flush(S);
+    rel = rn > 0 ? std::sqrt(*S->hnorm) / rn : 0.0;
+    if (stats && it < 256) stats->resid_hist[it] = rel;
+    if (!std::isfinite(rel)) {
+      result = CC_ERR_DIVERGED;
+      break;
+    }
+    if (rel < S->prm.rel_tol) {
+      result = CC_OK;
+      break;
+    }
+    if (it >= S->prm.max_iter) break;
+    if (use_graph) {
+      if (!S->cycle_exec) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
+        one_cycle(S);
+        CK(cudaStreamEndCapture(S->stream, &g));
+        CK(cudaGraphInstantiate(&S->cycle_exec, g, 0));
+        cudaGraphDestroy(g);
+      }
+      CK(cudaGraphLaunch(S->cycle_exec, S->stream));
+    } else {
+      one_cycle(S);
+    }
+    CK(cudaStreamSynchronize(S->stream));
+  }
+  {
+    ProfScope ps(S, P_SCATTER, 0.0);
+    if (S->nabs) k_absorbed<<<grid_for(S, S->nabs, 128), 128, 0, S->stream>>>(S->phi, S->nabs, S->a_cell, S->a_own);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, S->stream));
+  if (phi_out)
+    CK(cudaMemcpyAsync(phi_out, S->phi, L.N * sizeof(double),
+                       where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (S->prof) prof_flush(S);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = it;
+    stats->converged = result == CC_OK;
+    stats->rel_resid = rel;
+    stats->ms_solve = ms;
+  }
+  if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter";
+  if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  return result;
+}
+
+}  // namespace
+
+thread_local std::string g_setup_err;  // message of the last failed cc_setup on this thread
+
+extern "C" {
+
+void cc_default_params(cc_params* p) {
+  if (!p) return;
+  p->omega = 0.5;
+  p->nu1 = 3;
+  p->nu2 = 3;
+  p->max_iter = 200;
+  p->rel_tol = 1e-10;
+  p->min_coarse_n = 16;
+  p->max_levels = 16;
+  p->use_graph = 1;
+  p->lu_leaf = 64;
+  p->host_threads = 0;
+}
+
+const char* cc_status_str(cc_status st) {
+  switch (st) {
+    case CC_OK: return "ok";
+    case CC_ERR_INVALID_ARG: return "invalid argument";
+    case CC_ERR_OOM: return "out of memory";
+    case CC_ERR_CUDA: return "CUDA error";
+    case CC_ERR_PLG: return "no poised lattice (PLG) on the finest level";
+    case CC_ERR_SINGULAR: return "singular or tiny pivot in an LU factorisation";
+    case CC_ERR_NOT_CONVERGED: return "not converged";
+    case CC_ERR_DIVERGED: return "diverged";
+    case CC_ERR_MERGE: return "cell merging failed";
+    case CC_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+cc_status cc_last_error(const cc_solver* s, char* buf, int len) {
+  if (!buf || len <= 0) return CC_ERR_INVALID_ARG;
+  std::snprintf(buf, len, "%s", s ? s->err.c_str() : g_setup_err.c_str());
+  return CC_OK;
+}
+
+void cc_destroy(cc_solver* S) {
+  if (!S) return;
+  if (S->host_only) {
+    delete S;
+    return;
+  }
+  cudaSetDevice(S->device);
+  drop_graph(S);
+  for (void* p : S->allocs) cudaFree(p);
+  if (S->hnorm) cudaFreeHost(S->hnorm);
+  if (S->own_stream) cudaStreamDestroy(S->own_stream);
+  delete S;
+}
+
+cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solver** out) {
+  if (!g || !out || g->n < 8 || g->nshapes < 0 || (g->nshapes > 0 && !g->shapes)) return CC_ERR_INVALID_ARG;
+  *out = nullptr;
+  cc_solver* S = new cc_solver();
+  if (p)
+    S->prm = *p;
+  else
+    cc_default_params(&S->prm);
+  if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1) {
+    delete S;
+    return CC_ERR_INVALID_ARG;
+  }
+  std::memset(&S->info, 0, sizeof(S->info));
+  S->device = device;
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<Ellipsoid> shapes(g->nshapes);
+  for (int i = 0; i < g->nshapes; ++i)
+    for (int d = 0; d < 3; ++d) {
+      shapes[i].c[d] = g->shapes[i].centre[d];
+      shapes[i].a[d] = g->shapes[i].semi[d];
+    }
+  HierarchyParams hp;
+  hp.min_n = std::max(8, S->prm.min_coarse_n);
+  hp.max_levels = std::max(1, std::min(16, S->prm.max_levels));
+  std::string err;
+  int rc = build_hierarchy(S->host, g->n, shapes, g->shape_bc, g->box_bc, hp, &err);
+  if (rc) {
+    cc_status st = rc == 1 ? CC_ERR_PLG : (rc == 2 ? CC_ERR_MERGE : CC_ERR_INVALID_ARG);
+    g_setup_err = err;
+    delete S;
+    return st;
+  }
+  const int M = (int)S->host.size() - 1;
+  // factorisations (host)
+  std::vector<SuperLU> lus(S->host.size());
+  std::vector<std::vector<int>> lu_cells(S->host.size());
+  std::vector<std::vector<int>> rptr(S->host.size()), rcol(S->host.size());
+  std::vector<std::vector<double>> rval(S->host.size());
+  std::vector<StencilP> sp(S->host.size());
+  for (int m = 0; m <= M; ++m) {
+    const Level& L = S->host[m];
+    sp[m] = make_stencil(L);
+    if (m < M) {
+      // L22 over compact phi2 indices; L21 rows keep grid columns for the RHS kernel
+      const int n2 = (int)L.p2_cell.size();
+      std::vector<int> cid(L.typ.size(), -1);
+      for (int r = 0; r < n2; ++r) cid[L.p2_cell[r]] = r;
+      std::vector<int> ptr(1, 0), col, xyz;
+      std::vector<double> val;
+      rptr[m].assign(1, 0);
+      for (int r = 0; r < n2; ++r) {
+        for (int q = L.p2_ptr[r]; q < L.p2_ptr[r + 1]; ++q) {
+          int c = L.p2_col[q];
+          if (L.typ[c] == 2) {
+            col.push_back(cid[c]);
+            val.push_back(L.p2_val[q]);
+          } else {
+            rcol[m].push_back(c);
+            rval[m].push_back(L.p2_val[q]);
+          }
+        }
+        ptr.push_back((int)col.size());
+        rptr[m].push_back((int)rcol[m].size());
+        int c = L.p2_cell[r];
+        xyz.push_back(c / (L.n * L.n));
+        xyz.push_back((c / L.n) % L.n);
+        xyz.push_back(c % L.n);
+      }
+      if (factor_nd(ptr, col, val, xyz, lus[m], S->prm.lu_leaf, &err)) {
+        g_setup_err = "level " + std::to_string(m) + " LU-correction: " + err;
+        delete S;
+        return CC_ERR_SINGULAR;
+      }
+      lu_cells[m] = L.p2_cell;
+    } else {
+      std::vector<int> uid, ptr, col, xyz;
+      std::vector<double> val;
+      full_operator(L, sp[m], uid, lu_cells[m], ptr, col, val, xyz);
+      if (factor_nd(ptr, col, val, xyz, lus[m], S->prm.lu_leaf, &err)) {
+        g_setup_err = "bottom level: " + err;
+        delete S;
+        return CC_ERR_SINGULAR;
+      }
+      rptr[m].assign(lu_cells[m].size() + 1, 0);
+    }
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  if (device < 0) {  // host-only: setup queries work, GPU entry points are refused
+    S->host_only = true;
+    for (int m = 0; m <= M; ++m) {
+      const Level& L = S->host[m];
+      S->info.n[m] = L.n;
+      S->info.n_unknowns[m] = L.n_unknowns;
+      S->info.n_phi2[m] = (int)L.p2_cell.size();
+      S->info.lu_height[m] = lus[m].height;
+      S->info.lu_entries[m] = lus[m].nnz_factor;
+      S->info.phi2_nnz[m] = (long long)L.p2_col.size();
+    }
+    S->info.n_levels = M + 1;
+    finish_host_info(S);
+    S->info.ms_setup_host = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    *out = S;
+    return CC_OK;
+  }
+  // device
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete S;
+    return CC_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) S->nsm = prop.multiProcessorCount;
+  if (cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete S;
+    return CC_ERR_CUDA;
+  }
+  S->stream = S->own_stream;
+  cc_status st = CC_OK;
+#define TRY(x)            \
+  do {                    \
+    st = (x);             \
+    if (st) goto failed;  \
+  } while (0)
+  S->lev.resize(S->host.size());
+  for (int m = 0; m <= M; ++m) {
+    const Level& L = S->host[m];
+    DevLevel& D = S->lev[m];
+    D.n = L.n;
+    D.N = (long long)L.n * L.n * L.n;
+    D.P = sp[m];
+    TRY(dupload(S, &D.typ, L.typ));
+    D.n2 = (int)L.p2_cell.size();
+    D.p2_nnz = (long long)L.p2_col.size();
+    TRY(dupload(S, &D.p2_cell, L.p2_cell));
+    TRY(dupload(S, &D.p2_ptr, L.p2_ptr));
+    TRY(dupload(S, &D.p2_col, L.p2_col));
+    TRY(dupload(S, &D.p2_val, L.p2_val));
+    TRY(upload_lu(S, D.lu, lus[m], lu_cells[m], rptr[m], rcol[m], rval[m]));
+    TRY(dalloc(S, &D.s, D.N));
+    TRY(dalloc(S, &D.e, D.N));
+    TRY(dalloc(S, &D.tmp, D.N));
+    S->info.n[m] = L.n;
+    S->info.n_unknowns[m] = L.n_unknowns;
+    S->info.n_phi2[m] = D.n2;
+    S->info.lu_height[m] = lus[m].height;
+    S->info.lu_entries[m] = lus[m].nnz_factor;
+    S->info.phi2_nnz[m] = D.p2_nnz;
+  }
+  S->info.n_levels = M + 1;
+  {
+    const Level& L0 = S->host[0];
+    DevLevel& D0 = S->lev[0];
+    TRY(dalloc(S, &S->r, D0.N));
+    TRY(dalloc(S, &S->phi, D0.N));
+    TRY(dalloc(S, &S->s0, D0.N));
+    TRY(dalloc(S, &S->f, D0.N));
+    TRY(dalloc(S, &S->gbox, (size_t)6 * L0.n * L0.n));
+    TRY(dalloc(S, &S->norm, 1));
+    if (cudaMallocHost((void**)&S->hnorm, sizeof(double)) != cudaSuccess) {
+      st = CC_ERR_OOM;
+      goto failed;
+    }
+    std::vector<int> patch_of = finish_host_info(S);
+    TRY(dalloc(S, &S->gpatch, S->patch_owner.size()));
+    std::vector<int> bp(L0.p2_bpatch.size());
+    for (size_t q = 0; q < bp.size(); ++q) bp[q] = patch_of[L0.p2_bpatch[q]];
+    S->n2_0 = D0.n2;
+    TRY(dupload(S, &S->b_ptr, L0.p2_bptr));
+    TRY(dupload(S, &S->b_patch, bp));
+    TRY(dupload(S, &S->b_coef, L0.p2_bcoef));
+    // merged groups: volume weights; absorbed cells
+    std::vector<int> go, gp(1, 0), gpart, acell, aown;
+    std::vector<double> gw;
+    for (size_t gi = 0; gi < L0.groups.size(); ++gi) {
+      const auto& mem = L0.groups[gi];
+      if (mem.size() < 2) continue;
+      double tot = 0;
+      for (int c : mem) tot += L0.geo.vol[c];
+      go.push_back(mem[0]);
+      for (int c : mem) {
+        gpart.push_back(c);
+        gw.push_back(L0.geo.vol[c] / tot);
+        if (c != mem[0]) {
+          acell.push_back(c);
+          aown.push_back(mem[0]);
+        }
+      }
+      gp.push_back((int)gpart.size());
+    }
+    S->ngroups = (int)go.size();
+    S->nabs = (int)acell.size();
+    TRY(dupload(S, &S->g_owner, go));
+    TRY(dupload(S, &S->g_ptr, gp));
+    TRY(dupload(S, &S->g_part, gpart));
+    TRY(dupload(S, &S->g_w, gw));
+    TRY(dupload(S, &S->a_cell, acell));
+    TRY(dupload(S, &S->a_own, aown));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    st = CC_ERR_CUDA;
+    goto failed;
+  }
+  {
+    auto t2 = std::chrono::steady_clock::now();
+    S->info.ms_setup_host = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S->info.ms_setup_device = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  }
+  for (int k = 0; k < P_COUNT; ++k) {
+    S->prof_launch[k] = 0;
+    S->prof_ms[k] = 0;
+    S->prof_bytes[k] = 0;
+  }
+  *out = S;
+  return CC_OK;
+failed:
+  cc_destroy(S);
+  return st;
+#undef TRY
+}
+
+cc_status cc_set_stream(cc_solver* S, void* stream) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  drop_graph(S);
+  S->stream = stream ? (cudaStream_t)stream : S->own_stream;
+  return CC_OK;
+}
+
+cc_status cc_sync(cc_solver* S) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  CK(cudaStreamSynchronize(S->stream));
+  return CC_OK;
+}
+
+cc_status cc_query(const cc_solver* S, cc_info* info) {
+  if (!S || !info) return CC_ERR_INVALID_ARG;
+  *info = S->info;
+  return CC_OK;
+}
+
+cc_status cc_cell_map(const cc_solver* S, int level, int8_t* kind, uint8_t* typ, int32_t* owner, double* vol) {
+  if (!S || level < 0 || level >= (int)S->host.size()) return CC_ERR_INVALID_ARG;
+  const Level& L = S->host[level];
+  const size_t N = L.typ.size();
+  for (size_t i = 0; i < N; ++i) {
+    if (kind) kind[i] = L.geo.kind[i];
+    if (typ) typ[i] = L.typ[i];
+    if (owner) owner[i] = L.owner[i];
+    if (vol) vol[i] = L.geo.vol[i];
+  }
+  return CC_OK;
+}
+
+cc_status cc_cut_nodes(const cc_solver* S, int32_t* cells, int64_t* ptr, double* xyz, double* w) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  const Geometry& G = S->host[0].geo;
+  long long off = 0;
+  for (size_t c = 0; c < G.cut_cells.size(); ++c) {
+    if (cells) cells[c] = G.cut_cells[c];
+    if (ptr) ptr[c] = off;
+    const CutNodes& nd = G.nodes[c];
+    for (size_t q = 0; q < nd.vw.size(); ++q) {
+      if (xyz)
+        for (int d = 0; d < 3; ++d) xyz[3 * (off + q) + d] = nd.vp[3 * q + d];
+      if (w) w[off + q] = nd.vw[q];
+    }
+    off += (long long)nd.vw.size();
+  }
+  if (ptr) ptr[G.cut_cells.size()] = off;
+  return CC_OK;
+}
+
+cc_status cc_patch_nodes(const cc_solver* S, int32_t* owners, int64_t* ptr, double* xyz, double* w, double* normal) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  const Level& L = S->host[0];
+  const Geometry& G = L.geo;
+  long long off = 0;
+  for (size_t p = 0; p < S->patch_owner.size(); ++p) {
+    int o = S->patch_owner[p];
+    if (owners) owners[p] = o;
+    if (ptr) ptr[p] = off;
+    const auto& mem = L.groups[L.mom_id[o]];
+    for (int c : mem) {
+      int id = G.cut_id[c];
+      if (id < 0) continue;
+      const CutNodes& nd = G.nodes[id];
+      for (size_t q = 0; q < nd.sw.size(); ++q) {
+        if (xyz)
+          for (int d = 0; d < 3; ++d) xyz[3 * (off + q) + d] = nd.sp[3 * q + d];
+        if (normal)
+          for (int d = 0; d < 3; ++d) normal[3 * (off + q) + d] = nd.sn[3 * q + d];
+        if (w) w[off + q] = nd.sw[q];
+      }
+      off += (long long)nd.sw.size();
+    }
+  }
+  if (ptr) ptr[S->patch_owner.size()] = off;
+  return CC_OK;
+}
+
+cc_status cc_phi2_rows(const cc_solver* S, int level, int32_t* cells, int32_t* ptr, int32_t* cols, double* vals,
+                       int32_t* bptr, int32_t* bpatch, double* bcoef) {
+  if (!S || level < 0 || level >= (int)S->host.size()) return CC_ERR_INVALID_ARG;
+  const Level& L = S->host[level];
+  std::map<int, int> pnum;
+  for (size_t p = 0; p < S->patch_owner.size(); ++p) pnum[S->patch_owner[p]] = (int)p;
+  for (size_t r = 0; r < L.p2_cell.size(); ++r) {
+    if (cells) cells[r] = L.p2_cell[r];
+  }
+  for (size_t r = 0; r < L.p2_ptr.size(); ++r) {
+    if (ptr) ptr[r] = L.p2_ptr[r];
+    if (bptr) bptr[r] = L.p2_bptr[r];
+  }
+  for (size_t q = 0; q < L.p2_col.size(); ++q) {
+    if (cols) cols[q] = L.p2_col[q];
+    if (vals) vals[q] = L.p2_val[q];
+  }
+  for (size_t q = 0; q < L.p2_bpatch.size(); ++q) {
+    if (bpatch) bpatch[q] = level == 0 ? pnum[L.p2_bpatch[q]] : L.p2_bpatch[q];
+    if (bcoef) bcoef[q] = L.p2_bcoef[q];
+  }
+  return CC_OK;
+}
+
+cc_status cc_rhs(cc_solver* S, const double* f, const double* g_box, const double* g_patch, double* r, int where) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = build_rhs(S, f, g_box, g_patch, where);
+  if (st) return st;
+  if (r)
+    CK(cudaMemcpyAsync(r, S->r, S->lev[0].N * sizeof(double),
+                       where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return CC_OK;
+}
+
+cc_status cc_solve(cc_solver* S, const double* f, const double* g_box, const double* g_patch, double* phi,
+                   int where, cc_stats* stats) {
+  if (!S || !phi) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = build_rhs(S, f, g_box, g_patch, where);
+  if (st) return st;
+  DevLevel& L = S->lev[0];
+  CK(cudaMemcpyAsync(S->phi, phi, L.N * sizeof(double),
+                     where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
+  k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
+  return solve_loop(S, phi, where, stats);
+}
+
+cc_status cc_solve_r(cc_solver* S, const double* r, double* phi, int where, cc_stats* stats) {
+  if (!S || !r || !phi) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  DevLevel& L = S->lev[0];
+  cudaMemcpyKind k = where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(S->r, r, L.N * sizeof(double), k, S->stream));
+  CK(cudaMemcpyAsync(S->phi, phi, L.N * sizeof(double), k, S->stream));
+  k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->r, L.typ, L.N);
+  k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
+  return solve_loop(S, phi, where, stats);
+}
+
+cc_status cc_residual(cc_solver* S, int level, const double* phi, const double* rhs, double* out, int phi2_rows) {
+  if (!S || !phi || !rhs || !out) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  resid(S, S->lev[level], phi, rhs, out, phi2_rows != 0, nullptr);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_jacobi(cc_solver* S, int level, const double* phi_in, const double* rhs, double* phi_out) {
+  if (!S || !phi_in || !rhs || !phi_out || phi_in == phi_out) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  jacobi(S, S->lev[level], phi_in, rhs, phi_out);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_lu_correction(cc_solver* S, int level, double* phi, const double* rhs) {
+  if (!S || !phi || !rhs) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
+  lu_solve(S, S->lev[level].lu, rhs, phi);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_restrict_residual(cc_solver* S, int level, const double* phi, const double* rhs, double* coarse) {
+  if (!S || !phi || !rhs || !coarse) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  if (level + 1 >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "no coarser level");
+  restrict_resid(S, S->lev[level], phi, rhs, coarse);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_prolong_add(cc_solver* S, int level, const double* coarse, double* phi) {
+  if (!S || !phi || !coarse) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  if (level + 1 >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "no coarser level");
+  prolong(S, S->lev[level], coarse, phi);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_bottom_solve(cc_solver* S, const double* rhs, double* phi) {
+  if (!S || !rhs || !phi) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  DevLevel& L = S->lev.back();
+  CK(cudaMemsetAsync(phi, 0, L.N * sizeof(double), S->stream));
+  lu_solve(S, L.lu, rhs, phi);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_vcycle(cc_solver* S, const double* rhs, double* e) {
+  if (!S || !rhs || !e) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  vcycle_rec(S, 0, rhs, e);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_profile(cc_solver* S, int enable) {
+  if (!S) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  prof_flush(S);
+  S->prof = enable != 0;
+  if (S->prof) {
+    drop_graph(S);
+    for (int k = 0; k < P_COUNT; ++k) {
+      S->prof_launch[k] = 0;
+      S->prof_ms[k] = 0;
+      S->prof_bytes[k] = 0;
+    }
+  }
+  return CC_OK;
+}
+
+const char* cc_profile_entry(const cc_solver* S, int k, long long* launches, double* ms, double* bytes) {
+  if (!S || k < 0 || k >= P_COUNT) return nullptr;
+  if (launches) *launches = S->prof_launch[k];
+  if (ms) *ms = S->prof_ms[k];
+  if (bytes) *bytes = S->prof_bytes[k];
+  return kProfNames[k];
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+"""The C-ABI library builds, loads and exports every symbol include/ccmg.h declares.
+
+Also checks the host-only setup (device < 0) against the oracle on CPU: cell
+classes, merging, the phi1/phi2 split and every phi2 row of both levels of the
+sphere configuration at 32^3 (same columns, coefficients to 1e-12 relative).
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ccmg():
+    from paper_2410_05865_gb300 import build
+    build.build()
+    from paper_2410_05865_gb300 import ccmg as m
+    return m
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ccmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(ccmg):
+    L = ccmg.lib()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    # and the binding wraps each of them with a signature
+    assert set(names) == set(ccmg.SIGNATURES)
+
+
+def test_status_strings(ccmg):
+    L = ccmg.lib()
+    for st in range(10):
+        assert L.cc_status_str(st)
+
+
+def test_invalid_arguments(ccmg):
+    with pytest.raises(ccmg.CCError) as e:
+        ccmg.Solver(4, [], device=-1)
+    assert e.value.status == 1
+
+
+def test_setup_error_message(ccmg):
+    """A failed cc_setup leaves its reason for cc_last_error(NULL, ...)."""
+    bad = [((0.5, 0.5, 0.5), (0.2, -0.1, 0.2))]
+    with pytest.raises(ccmg.CCError) as e:
+        ccmg.Solver(16, bad, device=-1)
+    assert e.value.status == 1 and "semi-axis" in str(e.value)
+
+
+@pytest.fixture(scope="module")
+def host_pair(ccmg):
+    from oracle import discretization as D
+    prob = W.sphere_problem(32)
+    S = ccmg.Solver(32, prob.shapes, prob.shape_bc, prob.box_bc, device=-1)
+    levels = D.build_hierarchy(32, prob.shapes, prob.shape_bc, prob.box_bc)
+    return S, levels
+
+
+def test_host_setup_matches_oracle(host_pair):
+    S, levels = host_pair
+    assert S.levels == [lv.n for lv in levels]
+    for m, lv in enumerate(levels):
+        kind, typ, owner, vol = S.cell_map(m)
+        assert np.array_equal(kind, lv.kind)
+        assert np.array_equal(owner, lv.owner)
+        assert np.array_equal(typ, lv.typ)
+        assert np.abs(vol - lv.vol).max() < 1e-13
+        cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(m)
+        L = lv.L.tocsr()
+        for r, c in enumerate(cells):
+            u = lv.uid[c]
+            oc = lv.slots[L.indices[L.indptr[u]:L.indptr[u + 1]]]
+            ov = L.data[L.indptr[u]:L.indptr[u + 1]]
+            ref = dict(zip(oc, ov))
+            got = {}
+            for a, b in zip(cols[ptr[r]:ptr[r + 1]], vals[ptr[r]:ptr[r + 1]]):
+                got[a] = got.get(a, 0.0) + b
+            assert set(ref) == set(got)
+            scale = max(abs(v) for v in ref.values())
+            assert max(abs(ref[k] - got[k]) for k in ref) < 1e-12 * scale
+
+
+def test_host_patch_terms_match_oracle(host_pair, ccmg):
+    """Boundary coefficients of the phi2 rows (the N g part of r = f - N g)."""
+    S, levels = host_pair
+    lv = levels[0]
+    cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(0)
+    owners, _, _, _, _ = S.patch_nodes()
+    L = lv.L.tocsr()
+    for r, c in enumerate(cells):
+        u = lv.uid[c]
+        ref = {key[1]: v for key, v in lv.gcoef[u]}
+        got = {int(owners[bpatch[q]]): bcoef[q] for q in range(bptr[r], bptr[r + 1])}
+        assert set(ref) == set(got)
+        scale = np.abs(L.data[L.indptr[u]:L.indptr[u + 1]]).max()  # the row's scale
+        for k in ref:
+            assert abs(ref[k] - got[k]) < 1e-12 * scale

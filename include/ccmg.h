@@ -8,8 +8,8 @@
  * averages <<g>>_i on the irregular boundary (Sec. 2.3-2.4).  The discrete
  * system L phi = r := f - N g (Sec. 2.4) is solved by Alg. Multigrid with
  * Alg. VCycle (Sec. 5.3): omega-Jacobi on phi1 (SMO-1) + LU-correction on phi2
- * (SMO-2), volume-weighted restriction, piecewise-constant prolongation, and a
- * direct bottom solve.
+ * (SMO-2), restriction by the 2^-3 sum over phi1 children, piecewise-constant
+ * prolongation of the coarse phi1 corrections, and a direct bottom solve.
  *
  * Conventions
  *  - A grid array of level m has n_m^3 doubles, index (i*n_m + j)*n_m + k for
@@ -166,7 +166,8 @@ cc_status cc_jacobi(cc_solver* s, int level, const double* phi_in, const double*
 cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* rhs);
 /* Restrict: coarse[I] = 2^-3 sum of (rhs - L phi) over the phi1 children of I. */
 cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* coarse);
-/* Prolong: phi1 cells of `level` += coarse value of the parent. */
+/* Prolong: phi1 cells of `level` += coarse value of the parent, where the
+ * parent is a phi1 cell of level+1 (coarse phi2 cells prolongate nothing). */
 cc_status cc_prolong_add(cc_solver* s, int level, const double* coarse, double* phi);
 /* Bottom solver: phi = L^(M)^{-1} rhs on the coarsest level. */
 cc_status cc_bottom_solve(cc_solver* s, const double* rhs, double* phi);

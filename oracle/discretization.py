@@ -26,7 +26,12 @@ Readings where the paper is silent (each listed in the design doc):
 * phi1 needs every in-box cell of {i, i±e^d, i±2e^d} to be a full cell that
   takes part in no merge.
 * The PLG back-tracking of [PLG] is not in the paper; the lattice is the first
-  feasible one in a fixed preference order of per-axis coordinate orderings.
+  feasible one in a fixed preference order: stage 1 (eight per-axis
+  orderings, q at the lattice corner), stage 2 (q anywhere in a lattice inside
+  a 5^3 window: zig-zag orderings from every start).  A cell without a
+  degree-4 lattice is merged into a neighbour (up to 4 rounds).  On coarse
+  levels only, degrees 3 and 2 are then tried, and cells still without a
+  lattice are dropped from the coarse problem.
 * WLS weights 1 / (1 + |c_k - c_i|^2 / h^2) with c the centroids; one boundary
   row per lattice cell that carries a boundary patch.
 """
@@ -71,12 +76,54 @@ def _monos(degree):
     return [m for m in MONO if sum(m) <= degree]
 
 
-# per degree: (orderings, triples in preference order, lattice multi-indices)
+def _stage2_orderings(p):
+    """For every window {b..b+p} containing 0 and every start c0 in it, the
+    zig-zag c0, c0+s, c0-s, c0+2s, ... (s = +1, then -1) kept inside the window."""
+    out = []
+    for b in range(-p, 1):
+        for c0 in range(b, b + p + 1):
+            for s_ in (1, -1):
+                seq = [c0]
+                k = 1
+                while len(seq) < p + 1 and k <= 2 * p:
+                    for sg in (s_, -s_):
+                        v = c0 + sg * k
+                        if b <= v <= b + p and len(seq) < p + 1:
+                            seq.append(v)
+                    k += 1
+                seq = tuple(seq)
+                if seq not in out:
+                    out.append(seq)
+    return out
+
+
+def _stage2_triples(ords, p):
+    kz = [o.index(0) for o in ords]
+    ma = [max(abs(x) for x in o) for o in ords]
+    trip = [t for t in itertools.product(range(len(ords)), repeat=3) if kz[t[0]] + kz[t[1]] + kz[t[2]] <= p]
+    return sorted(trip, key=lambda t: (kz[t[0]] + kz[t[1]] + kz[t[2]], ma[t[0]] + ma[t[1]] + ma[t[2]], t))
+
+
+def _offsets(ords, triples, lattice):
+    """(ntriples, nlattice, 3) offsets of every candidate lattice."""
+    O = np.array([list(o) for o in ords])
+    T = np.array(triples)
+    K = np.array(lattice)
+    return np.stack([O[T[:, 0]][:, K[:, 0]], O[T[:, 1]][:, K[:, 1]], O[T[:, 2]][:, K[:, 2]]], axis=2)
+
+
+# per degree: [(orderings, triples, offsets) for stage 1 and stage 2], lattice multi-indices.
+# Stage 1: the fixed orderings with q at the lattice corner; stage 2: q anywhere
+# in a lattice inside a (p+1)^3 window, sorted by q's lattice index sum, then the
+# spread of the orderings.
 PLG_TABLES = {}
 for _p in (4, 3, 2):
-    _o = _orderings(_p)
-    _t = sorted(itertools.product(range(len(_o)), repeat=3), key=lambda t: (sum(t), t))
-    PLG_TABLES[_p] = (_o, _t, _monos(_p))
+    _lat = _monos(_p)
+    _o1 = _orderings(_p)
+    _t1 = sorted(itertools.product(range(len(_o1)), repeat=3), key=lambda t: (sum(t), t))
+    _o2 = _stage2_orderings(_p)
+    _t2 = _stage2_triples(_o2, _p)
+    PLG_TABLES[_p] = ([(_o1, _t1, _offsets(_o1, _t1, _lat)), (_o2, _t2, _offsets(_o2, _t2, _lat))], _lat)
 
 NEIGHBOURS = [(0, -1), (0, 1), (1, -1), (1, 1), (2, -1), (2, 1)]
 
@@ -187,9 +234,32 @@ class Level:
         self.kind = self.geo.kind
         self.vol = self.geo.vol
         self._merge()
+        self.excluded = np.zeros(n ** 3, dtype=bool)
         self._merged_moments()
         self._split()
-        self._rows()
+        failed = self._rows((4,))
+        # a cell without a degree-4 lattice is merged into a neighbour (up to 4 rounds)
+        for _ in range(4):
+            if not failed or self._merge_failed(failed) == 0:
+                break
+            self._merged_moments()
+            self._split()
+            failed = self._rows((4,))
+        if failed and coarse:
+            # coarse levels: degree 3, then 2; then cells still without a lattice
+            # are dropped from the coarse problem (zero correction there)
+            failed = self._rows((4, 3, 2))
+            for _ in range(32):
+                if not failed:
+                    break
+                self.excluded[failed] = True
+                owned = self.owner >= 0
+                self.excluded[owned] |= self.excluded[self.owner[owned]]
+                self._split()
+                failed = self._rows((4, 3, 2))
+        if failed:
+            c = tuple(int(x) for x in self.coords(failed[0]))
+            raise PLGError(f"no poised lattice for cell {c} at n={n}")
 
     # -------------------------------------------------------------- basics
     def coords(self, idx):
@@ -306,7 +376,7 @@ class Level:
     def _split(self):
         n = self.n
         N = n ** 3
-        clean = ((self.kind == 1) & ~self.merged).reshape(n, n, n)
+        clean = ((self.kind == 1) & ~self.merged & ~self.excluded).reshape(n, n, n)
         # out-of-box cells (ghosts) do not disqualify: pad with True
         pad = np.ones((n + 4, n + 4, n + 4), dtype=bool)
         pad[2:-2, 2:-2, 2:-2] = clean
@@ -317,31 +387,37 @@ class Level:
                 sl[d] = slice(2 + s_, n + 2 + s_)
                 ok &= pad[tuple(sl)]
         ok = ok.reshape(-1)
+        live = self.slot & ~self.excluded
         typ = np.zeros(N, dtype=np.int8)
-        typ[self.slot & ok] = 1
-        typ[self.slot & ~ok] = 2
+        typ[live & ok] = 1
+        typ[live & ~ok] = 2
         self.typ = typ
         self.uid = -np.ones(N, dtype=np.int64)
-        slots = np.nonzero(self.slot)[0]
+        slots = np.nonzero(live)[0]
         self.uid[slots] = np.arange(len(slots))
         self.slots = slots
         sp_ = np.zeros((n + 8, n + 8, n + 8), dtype=bool)
-        sp_[4:-4, 4:-4, 4:-4] = self.slot.reshape(n, n, n)
+        sp_[4:-4, 4:-4, 4:-4] = live.reshape(n, n, n)
         self._slotpad = sp_
 
     # ---------------------------------------------------------------- rows
-    def _rows(self):
-        n, h = self.n, self.h
+    def _rows(self, degrees=(4,)):
+        """Builds L over the unknowns; returns the phi2 cells without a lattice."""
         rows, cols, vals = [], [], []
         self.gcoef = {}
         self.plg = {}
+        failed = []
         for i in self.slots:
             i = int(i)
             r = int(self.uid[i])
             if self.typ[i] == 1:
                 ent, g = self.regular_row(i)
             else:
-                ent, g = self.plg_row(i)
+                res = self.plg_row(i, degrees)
+                if res is None:
+                    failed.append(i)
+                    continue
+                ent, g = res
             for j, v in ent.items():
                 rows.append(r)
                 cols.append(int(self.uid[j]))
@@ -350,6 +426,26 @@ class Level:
         N = len(self.slots)
         self.L = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
         self.L.sum_duplicates()
+        return failed
+
+    def _merge_failed(self, failed):
+        """Merge each cell without a lattice into its unknown face neighbour with
+        the largest common face (ties within AREA_TIE to the lowest index)."""
+        count = 0
+        for q in failed:
+            if self.owner[q] != q or not self.slot[q]:
+                continue
+            cand = [(j, self._area(q, j)) for j in self.neighbours(q)
+                    if self.slot[j] and self.owner[j] == j and not self.excluded[j]]
+            cand = [(j, a) for j, a in cand if a > 0.0]
+            if not cand:
+                continue
+            amax = max(a for _, a in cand)
+            best = min(j for j, a in cand if a >= amax - AREA_TIE)
+            self.owner[self.owner == q] = best
+            self.slot[q] = False
+            count += 1
+        return count
 
     def face_id(self, d, side, c):
         """Box face index: wall (2d+side) then the two tangential cell indices."""
@@ -386,29 +482,24 @@ class Level:
         return self.coords(o) + 0.5 + np.array([s[MONO_INDEX[(1, 0, 0)]], s[MONO_INDEX[(0, 1, 0)]],
                                                 s[MONO_INDEX[(0, 0, 1)]]]) / s[0]
 
-    def plg_row(self, q):
-        """First feasible triangular lattice (Def. PLG problem) and its WLS row.
+    def plg_row(self, q, degrees=(4,)):
+        """First feasible triangular lattice (Def. PLG problem) and its WLS row, or None.
 
-        The finest level needs degree 4.  On coarse levels (``self.coarse``) a
-        cell without any degree-4 lattice retries with degree 3, then 2."""
+        Degrees in ``degrees`` are tried in turn; for each, stage 1 then stage 2."""
         cq = self.coords(q)
         feas = self._slotpad[cq[0]:cq[0] + 9, cq[1]:cq[1] + 9, cq[2]:cq[2] + 9]
-        for degree in ((4, 3, 2) if self.coarse else (4,)):
-            ords, triples, lattice = PLG_TABLES[degree]
-            K = np.array(lattice)
-            for t in triples:
-                ox = np.array(ords[t[0]])[K[:, 0]]
-                oy = np.array(ords[t[1]])[K[:, 1]]
-                oz = np.array(ords[t[2]])[K[:, 2]]
-                if not np.all(feas[ox + 4, oy + 4, oz + 4]):
-                    continue
-                cells = [self.index(cq + np.array([a, b, c])) for a, b, c in zip(ox, oy, oz)]
-                row = self.wls_row(q, cells, degree)
-                if row is None:
-                    continue
-                self.plg[q] = (degree, t, cells)
-                return row
-        raise PLGError(f"no poised lattice for cell {tuple(int(x) for x in cq)} at n={self.n}")
+        for degree in degrees:
+            stages, lattice = PLG_TABLES[degree]
+            for ords, triples, offs in stages:
+                ok = np.all(feas[offs[:, :, 0] + 4, offs[:, :, 1] + 4, offs[:, :, 2] + 4], axis=1)
+                for t in np.nonzero(ok)[0]:
+                    cells = [self.index(cq + o) for o in offs[t]]
+                    row = self.wls_row(q, cells, degree)
+                    if row is None:
+                        continue
+                    self.plg[q] = (degree, triples[t], cells)
+                    return row
+        return None
 
     def wls_row(self, q, cells, degree=4):
         """Weighted LS fit in Pi_degree^3 over the lattice cells (+ boundary patches).

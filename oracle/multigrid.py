@@ -11,7 +11,8 @@ the permutation P of the nested-dissection ordering cancels
 Readings (listed in DESIGN.md): ||.|| is the Euclidean norm over all unknowns;
 Restrict is the printed 2^-D sum over the children with phi2 children (and
 cells that are not unknowns) contributing zero; Prolong adds the parent's
-value to phi1 cells only; a V-cycle starts from a zero correction on every
+value to phi1 cells only, and only from parents that are phi1 cells of the
+coarse level; a V-cycle starts from a zero correction on every
 level (Sec. 6.3 uses a zero initial guess).
 """
 from __future__ import annotations
@@ -90,11 +91,20 @@ def restrict(fine_ops, coarse_ops, pmap, t):
     return out
 
 
-def prolong(fine_ops, pmap, e_coarse, phi):
-    """Prolong: phi1 += the parent's value (patch-wise constant); phi2 unchanged."""
+def prolong(fine_ops, coarse_ops, pmap, e_coarse, phi, from_coarse_phi2=False):
+    """Prolong: phi1 += the parent's value (patch-wise constant).
+
+    Reading of "leaving the correction ... for cells in phi2 to zero": the
+    correction of a coarse phi2 cell is not prolongated, and fine phi2 cells
+    receive none (the LU-correction that follows sets them).  Alg. FMG
+    prolongates a whole solution, from every coarse unknown
+    (from_coarse_phi2=True)."""
     out = phi.copy()
+    ec = np.zeros_like(e_coarse)
+    keep = slice(None) if from_coarse_phi2 else coarse_ops.i1
+    ec[keep] = e_coarse[keep]
     p = pmap[fine_ops.i1]
-    out[fine_ops.i1] += np.where(p >= 0, e_coarse[np.maximum(p, 0)], 0.0)
+    out[fine_ops.i1] += np.where(p >= 0, ec[np.maximum(p, 0)], 0.0)
     return out
 
 
@@ -122,7 +132,7 @@ class Hierarchy:
         t = residual(ops, phi, s)
         sc = restrict(ops, self.ops[m + 1], self.pmaps[m], t)
         ec = self.vcycle(m + 1, sc)
-        phi = prolong(ops, self.pmaps[m], ec, phi)
+        phi = prolong(ops, self.ops[m + 1], self.pmaps[m], ec, phi)
         phi = smooth(ops, phi, s, self.omega, self.nu2)
         return phi
 
@@ -149,7 +159,8 @@ class Hierarchy:
             rs.append(restrict(self.ops[m], self.ops[m + 1], self.pmaps[m], rs[-1]))
         phi = self.bottom(rs[self.M])
         for m in range(self.M - 1, -1, -1):
-            phi = prolong(self.ops[m], self.pmaps[m], phi, np.zeros(len(rs[m])))
+            phi = prolong(self.ops[m], self.ops[m + 1], self.pmaps[m], phi, np.zeros(len(rs[m])),
+                          from_coarse_phi2=True)
             for _ in range(n_vcycles):
                 phi = phi + self.vcycle(m, rs[m] - self.ops[m].L @ phi)
         return phi

@@ -327,6 +327,30 @@ def cell_averages(solver: Solver, fn, q=8):
     return out
 
 
+def cell_averages_terms(solver: Solver, terms, q=8):
+    """cell_averages for f = sum_t coef_t fx_t(x) fy_t(y) fz_t(z): on full cells the
+    q^3 tensor Gauss-Legendre rule factorises into three 1-D rules."""
+    n = solver.n
+    h = 1.0 / n
+    kind, _, _, _ = solver.cell_map(0)
+    gx, gw = _gl(q)
+    pts = (np.arange(n)[:, None] + gx[None, :]) * h  # (n, q)
+    acc = np.zeros((n, n, n))
+    for coef, (fx, fy, fz) in terms:
+        ax = fx(pts) @ gw
+        ay = fy(pts) @ gw
+        az = fz(pts) @ gw
+        acc += coef * ax[:, None, None] * ay[None, :, None] * az[None, None, :]
+    out = np.where(kind == 1, acc.reshape(-1), 0.0)
+    cells, ptr, xyz, w = solver.cut_nodes()
+    if len(cells):
+        val = np.zeros(len(w))
+        for coef, (fx, fy, fz) in terms:
+            val += coef * fx(xyz[:, 0]) * fy(xyz[:, 1]) * fz(xyz[:, 2])
+        out[cells] = np.add.reduceat(val * w, ptr[:-1]) / np.add.reduceat(w, ptr[:-1])
+    return out
+
+
 def box_face_averages(solver: Solver, fn, grad, box_bc=(DIRICHLET,) * 6, q=8):
     """<g> on the 6 n^2 box faces: fn (Dirichlet walls) or d fn/d n (Neumann walls)."""
     n = solver.n

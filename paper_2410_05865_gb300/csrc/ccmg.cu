@@ -150,15 +150,18 @@ __global__ void k_restrict(const double* __restrict__ phi, const double* __restr
   }
 }
 
+// phi1 cells += the parent's correction, taken only from parents that are phi1
+// cells of the coarse level (a coarse phi2 cell prolongates no correction).
 __global__ void k_prolong(const double* __restrict__ coarse, double* __restrict__ phi,
-                          const uint8_t* __restrict__ typ, int n) {
+                          const uint8_t* __restrict__ typ, const uint8_t* __restrict__ typ_c, int n) {
   const long long N = (long long)n * n * n;
   const int nc = n / 2;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
     if (typ[idx] != 1) continue;
     const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
-    phi[idx] += coarse[((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1)];
+    const long long I = ((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
+    if (typ_c[I] == 1) phi[idx] += coarse[I];
   }
 }
 
@@ -643,10 +646,11 @@ void restrict_resid(cc_solver* S, DevLevel& L, const double* phi, const double* 
   k_restrict<<<grid_for(S, L.N / 8, block), block, 0, S->stream>>>(phi, s, coarse, L.typ, L.P);
 }
 
-void prolong(cc_solver* S, DevLevel& L, const double* coarse, double* phi) {
+void prolong(cc_solver* S, int m, const double* coarse, double* phi) {
+  DevLevel& L = S->lev[m];
   const int block = 256;
-  ProfScope ps(S, P_PROLONG, 17.125 * L.N);
-  k_prolong<<<grid_for(S, L.N, block), block, 0, S->stream>>>(coarse, phi, L.typ, L.n);
+  ProfScope ps(S, P_PROLONG, 17.25 * L.N);
+  k_prolong<<<grid_for(S, L.N, block), block, 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
 }
 
 void vcycle_rec(cc_solver* S, int m, const double* s, double* e) {
@@ -667,7 +671,7 @@ void vcycle_rec(cc_solver* S, int m, const double* s, double* e) {
   DevLevel& C = S->lev[m + 1];
   restrict_resid(S, L, cur, s, C.s);
   vcycle_rec(S, m + 1, C.s, C.e);
-  prolong(S, L, C.e, cur);
+  prolong(S, m, C.e, cur);
   for (int it = 0; it < S->prm.nu2; ++it) {
     jacobi(S, L, cur, s, oth);
     std::swap(cur, oth);
@@ -1296,7 +1300,7 @@ cc_status cc_prolong_add(cc_solver* S, int level, const double* coarse, double* 
   cc_status st = check_level(S, level);
   if (st) return st;
   if (level + 1 >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "no coarser level");
-  prolong(S, S->lev[level], coarse, phi);
+  prolong(S, level, coarse, phi);
   CK(cudaGetLastError());
   return CC_OK;
 }

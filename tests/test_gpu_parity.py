@@ -148,7 +148,7 @@ def test_transfer_parity(pair):
     g = dev(to_grid(f, phi))
     S.prolong_add(0, dev(to_grid(c, e)), g)
     S.sync()
-    ref = MG.prolong(H.ops[0], H.pmaps[0], e, phi)
+    ref = MG.prolong(H.ops[0], H.ops[1], H.pmaps[0], e, phi)
     assert rel(from_grid(f, g.cpu()), ref, np.abs(ref).max()) < 1e-14
 
 

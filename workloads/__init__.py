@@ -150,3 +150,31 @@ def rhs_field(problem: Problem):
         return lap_phi_exact
     b = problem.bumps
     return lambda x, y, z: lap_phi_exact(x, y, z) + bump_field(b, x, y, z)
+
+
+# ------------------------------------------------------ separable forms
+def _sin2pi(x):
+    return np.sin(TWO_PI * x)
+
+
+def phi_terms():
+    """phi_exact as a sum of separable products: [(coef, (fx, fy, fz))]."""
+    return [(1.0, (_sin2pi, _sin2pi, _sin2pi)), (0.1, (np.exp, np.exp, np.exp))]
+
+
+def rhs_terms(problem: Problem):
+    """f = Lap phi_exact (+ bumps) as a sum of separable products."""
+    terms = [(-3.0 * TWO_PI ** 2, (_sin2pi, _sin2pi, _sin2pi)), (0.3, (np.exp, np.exp, np.exp))]
+    if problem.bumps is not None:
+        b = problem.bumps
+        for a, w, c in zip(b["amp"], b["width"], b["centre"]):
+            fs = tuple((lambda x, cc=cc, ww=w: np.exp(-(x - cc) ** 2 / (2.0 * ww * ww))) for cc in c)
+            terms.append((float(a), fs))
+    return terms
+
+
+def eval_terms(terms, x, y, z):
+    out = 0.0
+    for coef, (fx, fy, fz) in terms:
+        out = out + coef * fx(x) * fy(y) * fz(z)
+    return out

@@ -174,6 +174,12 @@ cc_status cc_bottom_solve(cc_solver* s, const double* rhs, double* phi);
 /* e = VCycle(s) on level 0 (zero initial correction). */
 cc_status cc_vcycle(cc_solver* s, const double* rhs, double* e);
 
+/* Setup diagnostic (host-only solvers, device < 0): solves the level's
+ * LU-corrected block (bottom level: the whole L^(M)) with the stored factors
+ * on the host for a fixed test vector; returns ||A x - b|| / ||b|| and the
+ * smallest and largest pivot magnitudes of the factorisation. */
+cc_status cc_lu_check(const cc_solver* s, int level, double* rel_resid, double* min_pivot, double* max_pivot);
+
 /* Per-kernel timing of the next solves (CUDA events around every launch,
  * graphs off): enable != 0 starts and clears the counters. */
 cc_status cc_profile(cc_solver* s, int enable);

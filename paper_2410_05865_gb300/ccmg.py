@@ -86,6 +86,7 @@ SIGNATURES = {
     "cc_bottom_solve": (C.c_int, [_P, _P, _P]),
     "cc_vcycle": (C.c_int, [_P, _P, _P]),
     "cc_profile": (C.c_int, [_P, C.c_int]),
+    "cc_lu_check": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "cc_profile_entry": (C.c_char_p, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D]),
 }
 
@@ -229,9 +230,12 @@ class Solver:
         self._check(lib().cc_rhs(self._h, _ptr(f), _ptr(g_box), _ptr(g_patch), _ptr(out), where), "cc_rhs")
         return out
 
-    def solve(self, f, g_box, g_patch, phi):
-        """Alg. Multigrid; phi (initial guess, overwritten) is numpy (host) or a CUDA tensor."""
-        where = CC_HOST if isinstance(phi, np.ndarray) else CC_DEVICE
+    def solve(self, f, g_box, g_patch, phi, where=None):
+        """Alg. Multigrid; phi (initial guess, overwritten) is numpy (host) or a CUDA tensor.
+
+        ``where`` overrides the guess (CC_HOST for pinned CPU torch tensors)."""
+        if where is None:
+            where = CC_HOST if isinstance(phi, np.ndarray) or not phi.is_cuda else CC_DEVICE
         st = cc_stats()
         rc = lib().cc_solve(self._h, _ptr(f), _ptr(g_box), _ptr(g_patch), _ptr(phi), where, C.byref(st))
         if rc not in (0, 6):
@@ -276,6 +280,12 @@ class Solver:
 
     def vcycle(self, s, e):
         self._check(lib().cc_vcycle(self._h, _ptr(s), _ptr(e)), "cc_vcycle")
+
+    def lu_check(self, level):
+        """(||A x - b|| / ||b||, min pivot, max pivot) of a level's factors (host-only solvers)."""
+        r, a, b = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib().cc_lu_check(self._h, level, C.byref(r), C.byref(a), C.byref(b)), "cc_lu_check")
+        return r.value, a.value, b.value
 
     def profile(self, enable=True):
         self._check(lib().cc_profile(self._h, int(enable)), "cc_profile")

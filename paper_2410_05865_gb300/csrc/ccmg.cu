@@ -202,7 +202,7 @@ __global__ void k_tasks(const Task* __restrict__ tasks, int ntasks, const double
     const Task tk = tasks[t];
     const double* __restrict__ row = vals + tk.moff;
     double acc = 0.0;
-    if (MODE == T_B1) {
+    if (MODE == T_B1 || MODE == T_F1) {
       const int* __restrict__ g = gidx + tk.xoff;
       for (int j = lane; j < tk.ncols; j += 32) acc += row[j] * xin[g[j]];
     } else {
@@ -305,14 +305,17 @@ struct DevLU {
   int height = -1;
   double* vals = nullptr;
   int* structs = nullptr;
+  int* pivrow = nullptr;
   Task* tasks = nullptr;
   std::vector<long long> toff[4];  // per phase: offsets by height (height+2)
+  std::vector<double> tbytes[4];   // per phase and height: algorithmic bytes of one launch
   long long ntasks[4] = {0, 0, 0, 0};
   double *b = nullptr, *y = nullptr, *t = nullptr, *x = nullptr;
   int* cell = nullptr;  // ND position -> grid index
   int *rptr = nullptr, *rcol = nullptr;
   double* rval = nullptr;
   long long entries = 0;
+  long long rnnz = 0;
   long long task_bytes[4] = {0, 0, 0, 0};  // algorithmic bytes per solve phase (matrix + vectors)
 };
 
@@ -385,6 +388,10 @@ struct cc_solver {
   double prof_bytes[P_COUNT];
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<void*> allocs;
+  // host copies kept for diagnostics: per level the factored matrix (CSR) and factors
+  std::vector<SuperLU> host_lu;
+  std::vector<std::vector<int>> host_ptr, host_col;
+  std::vector<std::vector<double>> host_val;
 };
 
 namespace {
@@ -525,6 +532,7 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   cc_status st;
   if ((st = dupload(S, &D.vals, F.vals))) return st;
   if ((st = dupload(S, &D.structs, F.structs))) return st;
+  if ((st = dupload(S, &D.pivrow, F.pivrow))) return st;
   std::vector<Task> all;
   for (int ph = 0; ph < 4; ++ph) D.toff[ph].assign(F.height + 2, 0);
   std::vector<Task> per[4];
@@ -547,11 +555,15 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   }
   for (int ph = 0; ph < 4; ++ph) {
     long long bytes = 0;
+    D.tbytes[ph].assign(F.height + 1, 0.0);
     for (int h = 0; h <= F.height; ++h) {
       D.toff[ph][h] = (long long)all.size();
       for (const Task& t : byh[ph][h]) {
         all.push_back(t);
-        bytes += (long long)t.ncols * 8 * (ph == T_B1 ? 2 : 1) + 16;
+        // matrix row once (+ its gather indices for B1), plus the output element
+        long long b = (long long)t.ncols * ((ph == T_B1 || ph == T_F1) ? 12 : 8) + 8;
+        bytes += b;
+        D.tbytes[ph][h] += (double)b;
       }
     }
     D.toff[ph][F.height + 1] = (long long)all.size();
@@ -577,6 +589,7 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
     }
     rp.push_back((int)rc.size());
   }
+  D.rnnz = (long long)rc.size();
   if ((st = dupload(S, &D.rptr, rp))) return st;
   if ((st = dupload(S, &D.rcol, rc))) return st;
   if ((st = dupload(S, &D.rval, rv))) return st;
@@ -592,9 +605,9 @@ void launch_tasks(cc_solver* S, DevLU& D, int ph, int h) {
   int grid = grid_for(S, (long long)nt * 32, block);
   const Task* T = D.tasks + a;
   static const int cls[4] = {P_F1, P_F2, P_B1, P_B2};
-  ProfScope ps(S, cls[ph], 0.0);
+  ProfScope ps(S, cls[ph], D.tbytes[ph][h]);
   switch (ph) {
-    case T_F1: k_tasks<T_F1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.b, nullptr, nullptr, D.y); break;
+    case T_F1: k_tasks<T_F1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.b, D.pivrow, nullptr, D.y); break;
     case T_F2: k_tasks<T_F2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.y, nullptr, nullptr, D.b); break;
     case T_B1: k_tasks<T_B1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.x, D.structs, D.y, D.t); break;
     case T_B2: k_tasks<T_B2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.t, nullptr, nullptr, D.x); break;
@@ -606,7 +619,7 @@ void lu_solve(cc_solver* S, DevLU& D, const double* s, double* phi) {
   if (D.np == 0) return;
   const int block = 256;
   {
-    ProfScope ps(S, P_LURHS, 0.0);
+    ProfScope ps(S, P_LURHS, 8.0 * D.np + 12.0 * D.rnnz + 16.0 * D.np);
     k_lu_rhs<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.np, D.cell, D.rptr, D.rcol, D.rval, s, phi);
   }
   for (int h = 0; h <= D.height; ++h) {
@@ -617,7 +630,7 @@ void lu_solve(cc_solver* S, DevLU& D, const double* s, double* phi) {
     launch_tasks(S, D, T_B1, h);
     launch_tasks(S, D, T_B2, h);
   }
-  ProfScope ps(S, P_SCATTER, 0.0);
+  ProfScope ps(S, P_SCATTER, 16.0 * D.np);
   k_scatter<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
 }
 
@@ -930,6 +943,8 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   std::vector<std::vector<int>> rptr(S->host.size()), rcol(S->host.size());
   std::vector<std::vector<double>> rval(S->host.size());
   std::vector<StencilP> sp(S->host.size());
+  std::vector<std::vector<int>> mats_ptr(S->host.size()), mats_col(S->host.size());
+  std::vector<std::vector<double>> mats_val(S->host.size());
   for (int m = 0; m <= M; ++m) {
     const Level& L = S->host[m];
     sp[m] = make_stencil(L);
@@ -965,6 +980,9 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
         return CC_ERR_SINGULAR;
       }
       lu_cells[m] = L.p2_cell;
+      mats_ptr[m] = ptr;
+      mats_col[m] = col;
+      mats_val[m] = val;
     } else {
       std::vector<int> uid, ptr, col, xyz;
       std::vector<double> val;
@@ -974,10 +992,16 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
         delete S;
         return CC_ERR_SINGULAR;
       }
+      mats_ptr[m] = ptr;
+      mats_col[m] = col;
+      mats_val[m] = val;
       rptr[m].assign(lu_cells[m].size() + 1, 0);
     }
   }
   auto t1 = std::chrono::steady_clock::now();
+  S->host_ptr = std::move(mats_ptr);
+  S->host_col = std::move(mats_col);
+  S->host_val = std::move(mats_val);
   if (device < 0) {  // host-only: setup queries work, GPU entry points are refused
     S->host_only = true;
     for (int m = 0; m <= M; ++m) {
@@ -991,6 +1015,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     }
     S->info.n_levels = M + 1;
     finish_host_info(S);
+    S->host_lu = std::move(lus);
     S->info.ms_setup_host = std::chrono::duration<double, std::milli>(t1 - t0).count();
     *out = S;
     return CC_OK;
@@ -1336,6 +1361,29 @@ cc_status cc_profile(cc_solver* S, int enable) {
       S->prof_bytes[k] = 0;
     }
   }
+  return CC_OK;
+}
+
+cc_status cc_lu_check(const cc_solver* S, int level, double* rel_resid, double* min_pivot, double* max_pivot) {
+  if (!S || level < 0 || level >= (int)S->host_lu.size()) return CC_ERR_INVALID_ARG;
+  const SuperLU& F = S->host_lu[level];
+  const auto& ptr = S->host_ptr[level];
+  const auto& col = S->host_col[level];
+  const auto& val = S->host_val[level];
+  const int n = F.n;
+  std::vector<double> b(n), x;
+  for (int i = 0; i < n; ++i) b[i] = std::sin(1.0 + 0.37 * i);  // deterministic test vector
+  super_solve_host(F, b, x);
+  double rn = 0, bn = 0;
+  for (int i = 0; i < n; ++i) {
+    double a = 0;
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q) a += val[q] * x[col[q]];
+    rn += (a - b[i]) * (a - b[i]);
+    bn += b[i] * b[i];
+  }
+  if (rel_resid) *rel_resid = std::sqrt(rn / bn);
+  if (min_pivot) *min_pivot = F.min_pivot;
+  if (max_pivot) *max_pivot = F.max_pivot;
   return CC_OK;
 }
 

@@ -118,7 +118,7 @@ struct Rows1D {
 Rows1D regular_rows_1d(int bc_low, int bc_high, double h);
 
 // --------------------------------------------------------------- sparse LU
-// Supernodal LU (no pivoting) in a nested-dissection order, stored for the
+// Supernodal LU (partial pivoting inside supernodes) in a nested-dissection order, stored for the
 // GPU triangular solves: per supernode, explicit inverses of the diagonal
 // blocks, the dense off-diagonal blocks, and the row structure.
 struct SuperLU {
@@ -132,10 +132,15 @@ struct SuperLU {
   // value offsets (doubles) into vals for each supernode's blocks
   std::vector<long long> off_linv, off_uinv, off_l21, off_u12;
   std::vector<double> vals;
+  std::vector<int> pivrow;          // ND position read by row t of each supernode's forward step
   int height = 0;
   double min_pivot = 0, max_pivot = 0;
   long long nnz_factor = 0;         // entries stored (diag inverses + off-diagonal blocks)
 };
+
+// Host solve with the stored factors, in the same order the GPU uses
+// (x = P^T U^{-1} L^{-1} P b); b and x in the original numbering.
+void super_solve_host(const SuperLU& F, const std::vector<double>& b, std::vector<double>& x);
 
 // A is square CSR (n x n) with coordinates per row for the geometric ND.
 // Returns 0, or 1 if a pivot was zero / tiny (relative 1e-14).

@@ -8,7 +8,9 @@
 // are ordered recursively and the separator last (Alg. ND numbers separators
 // last).  Each leaf and each separator is one supernode.
 //
-// Factorisation: multifrontal, no pivoting (as the paper factors L22' = P L22 P^T).
+// Factorisation: multifrontal, with partial pivoting restricted to the fully
+// summed rows of each supernode (the paper factors L22' = P L22 P^T without
+// pivoting; that loses accuracy at 256^3, see the LU check of the setup).
 // For the GPU solves each supernode s stores inv(L_ss) (unit lower), inv(U_ss),
 // the dense block L_{struct(s), s} and U_{s, struct(s)}.
 #include <omp.h>
@@ -98,15 +100,31 @@ struct NdBuilder {
 };
 
 // ------------------------------------------------------------ dense kernels
-// Partial LU (no pivoting) of the first k columns of the row-major F x F front.
+// Partial LU of the first k columns of the row-major F x F front, with partial
+// pivoting among the k fully summed rows (rowperm[t] = front row moved to t).
 // Returns false on a zero pivot.  Blocked right-looking; trailing updates
 // parallel over rows when par is true.
-bool partial_lu(double* Fm, int F, int k, bool par, double* pmin, double* pmax) {
+bool partial_lu(double* Fm, int F, int k, bool par, double* pmin, double* pmax, int* rowperm) {
   const int nb = 48;
+  for (int t = 0; t < k; ++t) rowperm[t] = t;
   for (int j0 = 0; j0 < k; j0 += nb) {
     int j1 = std::min(k, j0 + nb);
     // panel: columns j0..j1 over rows j0..F (unblocked), updating panel columns only
     for (int j = j0; j < j1; ++j) {
+      // partial pivoting among the fully summed rows j..k-1 of this supernode
+      int p = j;
+      double best = std::fabs(Fm[(long long)j * F + j]);
+      for (int i = j + 1; i < k; ++i) {
+        double v = std::fabs(Fm[(long long)i * F + j]);
+        if (v > best) {
+          best = v;
+          p = i;
+        }
+      }
+      if (p != j) {
+        std::swap_ranges(Fm + (long long)j * F, Fm + (long long)(j + 1) * F, Fm + (long long)p * F);
+        std::swap(rowperm[j], rowperm[p]);
+      }
       double piv = Fm[(long long)j * F + j];
       if (piv == 0.0 || !std::isfinite(piv)) return false;
       *pmin = std::min(*pmin, std::fabs(piv));
@@ -176,6 +194,46 @@ void tri_inverses(const double* Fm, int F, int k, double* Linv, double* Uinv, bo
 }
 
 }  // namespace
+
+void super_solve_host(const SuperLU& F, const std::vector<double>& b, std::vector<double>& x) {
+  const int n = F.n;
+  std::vector<double> w(n), y(n), t(n), z(n);
+  for (int p = 0; p < n; ++p) w[p] = b[F.perm[p]];
+  for (int s = 0; s < F.nsuper; ++s) {  // forward, supernodes in postorder
+    const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+    const long long m = F.sn_struct[s + 1] - F.sn_struct[s];
+    const double* Li = &F.vals[F.off_linv[s]];
+    for (int r = 0; r < k; ++r) {
+      double a = 0;
+      for (int c = 0; c <= r; ++c) a += Li[(long long)r * k + c] * w[F.pivrow[f0 + c]];
+      y[f0 + r] = a;
+    }
+    const double* L21 = &F.vals[F.off_l21[s]];
+    for (long long a = 0; a < m; ++a) {
+      double v = 0;
+      for (int c = 0; c < k; ++c) v += L21[a * k + c] * y[f0 + c];
+      w[F.structs[F.sn_struct[s] + a]] -= v;
+    }
+  }
+  for (int s = F.nsuper - 1; s >= 0; --s) {  // backward
+    const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+    const long long m = F.sn_struct[s + 1] - F.sn_struct[s];
+    const double* U12 = &F.vals[F.off_u12[s]];
+    for (int r = 0; r < k; ++r) {
+      double v = 0;
+      for (long long a = 0; a < m; ++a) v += U12[r * m + a] * z[F.structs[F.sn_struct[s] + a]];
+      t[f0 + r] = y[f0 + r] - v;
+    }
+    const double* Ui = &F.vals[F.off_uinv[s]];
+    for (int r = 0; r < k; ++r) {
+      double a = 0;
+      for (int c = r; c < k; ++c) a += Ui[(long long)r * k + c] * t[f0 + c];
+      z[f0 + r] = a;
+    }
+  }
+  x.assign(n, 0.0);
+  for (int p = 0; p < n; ++p) x[F.perm[p]] = z[p];
+}
 
 int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const std::vector<double>& val,
               const std::vector<int>& coords, SuperLU& out, int leaf_size, std::string* err) {
@@ -309,6 +367,7 @@ int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const st
   }
   out.vals.assign(off, 0.0);
   out.nnz_factor = off;
+  out.pivrow.assign(n, 0);
   // numeric, by height so that independent fronts run in parallel
   std::vector<std::vector<double>> upd(ns);  // Schur complements waiting for the parent
   int bad = 0;
@@ -354,12 +413,13 @@ int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const st
         std::vector<double>().swap(upd[c]);
       }
       double lmin = 1e300, lmax = 0;
-      if (!partial_lu(Fm.data(), F, kk, !many, &lmin, &lmax)) {
+      if (!partial_lu(Fm.data(), F, kk, !many, &lmin, &lmax, &out.pivrow[f0])) {
         bad += 1;
         continue;
       }
       gmin = std::min(gmin, lmin);
       gmax = std::max(gmax, lmax);
+      for (int t = 0; t < kk; ++t) out.pivrow[f0 + t] += f0;  // ND positions
       double* Linv = &out.vals[out.off_linv[k]];
       double* Uinv = &out.vals[out.off_uinv[k]];
       tri_inverses(Fm.data(), F, kk, Linv, Uinv, !many);

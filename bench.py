@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-n", type=int, default=64, help="grid of the oracle's CPU sample")
+    ap.add_argument("--precision", type=int, default=1, help="0 FP64 V-cycle, 1 FP32 grid work + FP64 LU/outer")
+    ap.add_argument("--krylov", type=int, default=1, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
+    ap.add_argument("--min-n", type=int, default=32, help="coarsening stops before n < min-n")
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--no-fp64-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -223,7 +228,9 @@ def run_ours(args):
     n = args.n
     prob = W.ellipsoids_problem(n, args.seed)
     t0 = time.time()
-    S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local)
+    solver_kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n,
+                     krylov_restart=args.restart, max_iter=2000)
+    S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **solver_kw)
     setup_s = time.time() - t0
     stream = torch.cuda.Stream()
     S.set_stream(stream)
@@ -299,10 +306,27 @@ def run_ours(args):
     total_ms = sum(v[1] for v in prof.values())
     shares = {k: round(v[1] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]}
 
+    # the same solve with the FP64 V-cycle (the plain-FP64 reference of the metric)
+    fp64 = None
+    if args.precision != 0 and not args.no_fp64_reference:
+        kw = dict(solver_kw, precision=0)
+        S64 = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **kw)
+        S64.set_stream(stream)
+        with torch.cuda.stream(stream):
+            phi.zero_()
+            S64.solve(fd, gbd, gpd, phi)
+            phi.zero_()
+            st64, rc64 = S64.solve(fd, gbd, gpd, phi)
+        torch.cuda.synchronize()
+        fp64 = {"ms": st64.ms_solve, "v_cycles": st64.iters, "converged": bool(st64.converged),
+                "mdof_s": N / (st64.ms_solve / 1e3) / 1e6}
+        S64.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         small = W.ellipsoids_problem(args.cpu_n, args.seed)
-        Ss = ccmg.Solver(args.cpu_n, small.shapes, small.shape_bc, small.box_bc, device=local)
+        Ss = ccmg.Solver(args.cpu_n, small.shapes, small.shape_bc, small.box_bc, device=local,
+                         **dict(solver_kw, precision=0, krylov=0, min_coarse_n=16))
         fs, gbs, gps = make_inputs(ccmg, W, Ss, small)
         phs = torch.zeros(args.cpu_n ** 3, dtype=torch.float64, device="cuda")
         st_s, _ = Ss.solve(dev(fs), dev(gbs), dev(gps), phs)
@@ -321,6 +345,9 @@ def run_ours(args):
                        "phi2_per_level": [info.n_phi2[m] for m in range(info.n_levels)],
                        "lu_entries_per_level": [info.lu_entries[m] for m in range(info.n_levels)],
                        "v_cycles": iters[-1], "omega": 0.5, "nu1": 3, "nu2": 3,
+                       "precision": ["fp64", "fp32 grid work, fp64 LU-corrections/outer residual"][args.precision],
+                       "outer": ["Alg. Multigrid", f"GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
+                       "plain_fp64_same_solver": fp64,
                        "setup_s": round(setup_s, 1), "parallelism": f"replicas x{world}",
                        "l2": "no flush: working set of several GB > 129 MB L2"},
             "e2e": {"value": N * world / (ms_e / 1e3) / 1e6, "unit": "MDOF/s", "ms_per_step": ms_e,

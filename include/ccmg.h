@@ -77,6 +77,14 @@ typedef struct {
   int use_graph;     /* capture each V-cycle + outer update in a CUDA graph (1) */
   int lu_leaf;       /* nested-dissection leaf size (64) */
   int host_threads;  /* OpenMP threads for the setup (0 = default) */
+  int krylov;        /* 0: Alg. Multigrid (stationary, the paper); 1: restarted GMRES
+                        right-preconditioned by the same V-cycle (0) */
+  int krylov_restart;/* GMRES restart length m (30) */
+  int precision;     /* 0: FP64 V-cycle; 1: FP32 grid work inside the V-cycle (Jacobi,
+                        restriction, prolongation) with FP64 LU-corrections, bottom
+                        solve and outer residual (defect correction) (0) */
+  int lu_persistent; /* 1: each triangular solve is one launch with dynamic task fetch
+                        and bounded waits; 0: one launch per tree height and phase (1) */
 } cc_params;
 
 typedef struct {
@@ -150,7 +158,9 @@ cc_status cc_phi2_rows(const cc_solver* s, int level, int32_t* cells, int32_t* p
 cc_status cc_rhs(cc_solver* s, const double* f, const double* g_box, const double* g_patch, double* r, int where);
 
 /* Alg. Multigrid from the initial guess in phi (zero if all zeros), until
- * ||s||/||r|| < rel_tol or max_iter V-cycles.  phi receives the result.
+ * ||s||/||r|| < rel_tol or max_iter V-cycles.  phi receives the result.  With
+ * params.krylov = 1 the same V-cycle preconditions restarted GMRES instead
+ * (stats.iters counts V-cycles; the stop test uses the true residual). 
  * Returns CC_ERR_NOT_CONVERGED (phi = last iterate) or CC_ERR_DIVERGED. */
 cc_status cc_solve(cc_solver* s, const double* f, const double* g_box, const double* g_patch, double* phi,
                    int where, cc_stats* stats);
@@ -171,7 +181,7 @@ cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const
 cc_status cc_prolong_add(cc_solver* s, int level, const double* coarse, double* phi);
 /* Bottom solver: phi = L^(M)^{-1} rhs on the coarsest level. */
 cc_status cc_bottom_solve(cc_solver* s, const double* rhs, double* phi);
-/* e = VCycle(s) on level 0 (zero initial correction). */
+/* e = VCycle(s) on level 0 (zero initial correction), in the solver's precision. */
 cc_status cc_vcycle(cc_solver* s, const double* rhs, double* e);
 
 /* Setup diagnostic (host-only solvers, device < 0): solves the level's

@@ -33,7 +33,9 @@ Readings where the paper is silent (each listed in the design doc):
   levels only, degrees 3 and 2 are then tried, and cells still without a
   lattice are dropped from the coarse problem.
 * WLS weights 1 / (1 + |c_k - c_i|^2 / h^2) with c the centroids; one boundary
-  row per lattice cell that carries a boundary patch.
+  row per lattice cell that carries a boundary patch.  A fit whose own-cell
+  coefficient is not negative is rejected like a rank-deficient one (slivers
+  next to Neumann boundaries otherwise give wrong-signed rows).
 """
 from __future__ import annotations
 
@@ -559,6 +561,8 @@ class Level:
         ent = {}
         for j, b in zip(cells, beta[:nc]):
             ent[j] = ent.get(j, 0.0) + b
+        if not ent.get(q, 0.0) < 0.0:
+            return None  # a Laplacian row needs a negative diagonal: reject this fit
         g = []
         for j, b in zip(bnd, beta[nc:]):
             g.append((("patch", j), b * (h if self.shape_bc == NEUMANN else 1.0)))

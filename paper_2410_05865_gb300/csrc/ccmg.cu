@@ -33,79 +33,71 @@ struct StencilP {
   double inv12h2;
   double c[3][5][7];  // per axis, position class, offsets -3..3 (times 12 h^2)
   double g[3][5];     // coefficient of the nearer wall's <g> (times 12 h^2)
+  double winv[5][5][5];  // omega / D for each combination of position classes
 };
 
 __device__ __forceinline__ int pos_class(int p, int n) {
   return p == 0 ? 0 : (p == 1 ? 1 : (p == n - 2 ? 3 : (p == n - 1 ? 4 : 2)));
 }
 
-// (L phi)_i for a phi1 cell and the diagonal of its row.
-__device__ __forceinline__ double apply_regular(const double* __restrict__ phi, int i, int j, int k,
-                                                const StencilP& P, double* diag) {
+// (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
+template <class T>
+__device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int j, int k, const StencilP& P) {
   const int n = P.n;
   const long long nn = (long long)n * n;
   const long long idx = (long long)i * nn + (long long)j * n + k;
   const int ci = pos_class(i, n), cj = pos_class(j, n), ck = pos_class(k, n);
   if (ci == 2 && cj == 2 && ck == 2) {
-    const double c0 = phi[idx];
-    double s1 = phi[idx + nn] + phi[idx - nn] + phi[idx + n] + phi[idx - n] + phi[idx + 1] + phi[idx - 1];
-    double s2 = phi[idx + 2 * nn] + phi[idx - 2 * nn] + phi[idx + 2 * n] + phi[idx - 2 * n] + phi[idx + 2] +
-                phi[idx - 2];
-    *diag = -90.0 * P.inv12h2;
-    return (16.0 * s1 - s2 - 90.0 * c0) * P.inv12h2;
+    const T c0 = phi[idx];
+    T s1 = phi[idx + nn] + phi[idx - nn] + phi[idx + n] + phi[idx - n] + phi[idx + 1] + phi[idx - 1];
+    T s2 = phi[idx + 2 * nn] + phi[idx - 2 * nn] + phi[idx + 2 * n] + phi[idx - 2 * n] + phi[idx + 2] + phi[idx - 2];
+    return (T(16) * s1 - s2 - T(90) * c0) * T(P.inv12h2);
   }
   const int cls[3] = {ci, cj, ck};
   const long long stride[3] = {nn, (long long)n, 1};
-  double acc = 0.0, dg = 0.0;
+  T acc = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double* c = P.c[d][cls[d]];
 #pragma unroll
     for (int o = -3; o <= 3; ++o) {
       const double w = c[o + 3];
-      if (w != 0.0) acc += w * phi[idx + o * stride[d]];
+      if (w != 0.0) acc += T(w) * phi[idx + o * stride[d]];
     }
-    dg += c[3];
   }
-  *diag = dg * P.inv12h2;
-  return acc * P.inv12h2;
+  return acc * T(P.inv12h2);
 }
 
-__global__ void k_jacobi(const double* __restrict__ phi_in, const double* __restrict__ s,
-                         double* __restrict__ phi_out, const uint8_t* __restrict__ typ, StencilP P, double omega) {
+// Grid kernels run on a 3-D launch: threads along k, blockIdx.y = j, blockIdx.z = i.
+template <class T>
+__global__ void k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s, T* __restrict__ phi_out,
+                         const uint8_t* __restrict__ typ, StencilP P) {
   const int n = P.n;
-  const long long N = (long long)n * n * n;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const double v = phi_in[idx];
-    if (typ[idx] == 1) {
-      const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
-      double dg;
-      const double lphi = apply_regular(phi_in, i, j, k, P, &dg);
-      phi_out[idx] = v + omega * (s[idx] - lphi) / dg;
-    } else {
-      phi_out[idx] = v;
-    }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const long long idx = ((long long)i * n + j) * n + k;
+  const T v = phi_in[idx];
+  if (typ[idx] == 1) {
+    const T lphi = apply_regular<T>(phi_in, i, j, k, P);
+    // omega / D from the class table: one multiply instead of a divide
+    phi_out[idx] = fma(T(P.winv[pos_class(i, n)][pos_class(j, n)][pos_class(k, n)]), s[idx] - lphi, v);
+  } else {
+    phi_out[idx] = v;
   }
 }
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
   const int n = P.n;
-  const long long N = (long long)n * n * n;
-  double acc = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    double r = 0.0;
-    if (typ[idx] == 1) {
-      const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
-      double dg;
-      r = s[idx] - apply_regular(phi, i, j, k, P, &dg);
-    }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  double r = 0.0;
+  if (k < n) {
+    const long long idx = ((long long)i * n + j) * n + k;
+    if (typ[idx] == 1) r = s[idx] - apply_regular<double>(phi, i, j, k, P);
     out[idx] = r;
-    acc += r * r;
   }
   if (norm2) {
+    double acc = r * r;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(norm2, acc);
   }
@@ -128,56 +120,63 @@ __global__ void k_resid2(const double* __restrict__ phi, const double* __restric
   }
 }
 
-// coarse[I] = 2^-3 sum over the phi1 children of (s - L phi)
-__global__ void k_restrict(const double* __restrict__ phi, const double* __restrict__ s,
-                           double* __restrict__ coarse, const uint8_t* __restrict__ typ, StencilP P) {
+// coarse[I] = 2^-3 sum over the phi1 children of (s - L phi); 3-D launch over coarse cells
+template <class T>
+__global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T* __restrict__ coarse,
+                           const uint8_t* __restrict__ typ, StencilP P) {
   const int n = P.n, nc = n / 2;
-  const long long Nc = (long long)nc * nc * nc;
-  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
-       I += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(I / ((long long)nc * nc)), b = (int)((I / nc) % nc), c = (int)(I % nc);
-    double acc = 0.0;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y, a = blockIdx.z;
+  if (c >= nc) return;
+  T acc = 0;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int i = 2 * a + (t >> 2), j = 2 * b + ((t >> 1) & 1), k = 2 * c + (t & 1);
-      const long long idx = ((long long)i * n + j) * n + k;
-      if (typ[idx] == 1) {
-        double dg;
-        acc += s[idx] - apply_regular(phi, i, j, k, P, &dg);
-      }
-    }
-    coarse[I] = 0.125 * acc;
+  for (int t = 0; t < 8; ++t) {
+    const int i = 2 * a + (t >> 2), j = 2 * b + ((t >> 1) & 1), k = 2 * c + (t & 1);
+    const long long idx = ((long long)i * n + j) * n + k;
+    if (typ[idx] == 1) acc += s[idx] - apply_regular<T>(phi, i, j, k, P);
   }
+  coarse[((long long)a * nc + b) * nc + c] = T(0.125) * acc;
 }
 
 // phi1 cells += the parent's correction, taken only from parents that are phi1
 // cells of the coarse level (a coarse phi2 cell prolongates no correction).
-__global__ void k_prolong(const double* __restrict__ coarse, double* __restrict__ phi,
-                          const uint8_t* __restrict__ typ, const uint8_t* __restrict__ typ_c, int n) {
-  const long long N = (long long)n * n * n;
+template <class T>
+__global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
+                          const uint8_t* __restrict__ typ_c, int n) {
   const int nc = n / 2;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    if (typ[idx] != 1) continue;
-    const int i = (int)(idx / ((long long)n * n)), j = (int)((idx / n) % n), k = (int)(idx % n);
-    const long long I = ((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
-    if (typ_c[I] == 1) phi[idx] += coarse[I];
-  }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const long long idx = ((long long)i * n + j) * n + k;
+  if (typ[idx] != 1) return;
+  const long long I = ((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
+  if (typ_c[I] == 1) phi[idx] += coarse[I];
 }
 
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
+// (FP64 accumulation whatever the grid type: the LU-correction stays FP64)
+template <class T>
 __global__ void k_lu_rhs(double* __restrict__ b, int np, const int* __restrict__ cell, const int* __restrict__ ptr,
-                         const int* __restrict__ col, const double* __restrict__ val,
-                         const double* __restrict__ s, const double* __restrict__ phi) {
+                         const int* __restrict__ col, const double* __restrict__ val, const T* __restrict__ s,
+                         const T* __restrict__ phi) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    double v = s[cell[p]];
-    for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * phi[col[q]];
+    double v = (double)s[cell[p]];
+    for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
     b[p] = v;
   }
 }
 
-__global__ void k_scatter(const double* __restrict__ x, int np, const int* __restrict__ cell, double* __restrict__ phi) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) phi[cell[p]] = x[p];
+template <class T>
+__global__ void k_scatter(const double* __restrict__ x, int np, const int* __restrict__ cell, T* __restrict__ phi) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) phi[cell[p]] = (T)x[p];
+}
+
+__global__ void k_to_float(float* __restrict__ out, const double* __restrict__ in, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+__global__ void k_axpy_f(double* __restrict__ phi, const float* __restrict__ e, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    phi[i] += (double)e[i];
 }
 
 struct Task {
@@ -222,6 +221,185 @@ __global__ void k_tasks(const Task* __restrict__ tasks, int ntasks, const double
   }
 }
 
+// ---- fused supernode solves: one CTA runs both phases of a small supernode
+// (diagonal-block product into shared memory, then the off-diagonal block).
+constexpr int kSmallK = 256;  // supernodes with at most this many columns are "small"
+
+struct SnMeta {
+  long long linv, uinv, l21, u12, st;  // value offsets and struct offset
+  int first, k, m, pad;
+};
+
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+__device__ void fwd_one(const SnMeta& sm, const double* __restrict__ vals, const int* __restrict__ structs,
+                        const int* __restrict__ pivrow, double* b, double* __restrict__ y, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int k = sm.k, f0 = sm.first;
+  for (int t = warp; t < k; t += nw) {
+    const double* row = vals + sm.linv + (long long)t * k;
+    double a = 0.0;
+    for (int c = lane; c <= t; c += 32) a += row[c] * b[pivrow[f0 + c]];
+    a = warp_sum(a);
+    if (lane == 0) {
+      y[f0 + t] = a;
+      sh[t] = a;
+    }
+  }
+  __syncthreads();
+  for (int r = warp; r < sm.m; r += nw) {
+    const double* row = vals + sm.l21 + (long long)r * k;
+    double a = 0.0;
+    for (int c = lane; c < k; c += 32) a += row[c] * sh[c];
+    a = warp_sum(a);
+    if (lane == 0) atomicAdd(b + structs[sm.st + r], -a);
+  }
+  __syncthreads();
+}
+
+__device__ void bwd_one(const SnMeta& sm, const double* __restrict__ vals, const int* __restrict__ structs,
+                        const double* __restrict__ y, double* x, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int k = sm.k, f0 = sm.first, m = sm.m;
+  for (int r = warp; r < k; r += nw) {
+    const double* row = vals + sm.u12 + (long long)r * m;
+    double a = 0.0;
+    for (int c = lane; c < m; c += 32) a += row[c] * x[structs[sm.st + c]];
+    a = warp_sum(a);
+    if (lane == 0) sh[r] = y[f0 + r] - a;
+  }
+  __syncthreads();
+  for (int r = warp; r < k; r += nw) {
+    const double* row = vals + sm.uinv + (long long)r * k;
+    double a = 0.0;
+    for (int c = r + lane; c < k; c += 32) a += row[c] * sh[c];
+    a = warp_sum(a);
+    if (lane == 0) x[f0 + r] = a;
+  }
+  __syncthreads();
+}
+
+// one CTA per subtree (a contiguous postorder range [lo, hi] of small supernodes)
+__global__ void k_lu_subtree_fwd(const SnMeta* __restrict__ meta, const int2* __restrict__ ranges, int nr,
+                                 const double* __restrict__ vals, const int* __restrict__ structs,
+                                 const int* __restrict__ pivrow, double* b, double* __restrict__ y) {
+  __shared__ double sh[kSmallK];
+  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
+    const int2 rg = ranges[r];
+    for (int s = rg.x; s <= rg.y; ++s) fwd_one(meta[s], vals, structs, pivrow, b, y, sh);
+  }
+}
+
+__global__ void k_lu_subtree_bwd(const SnMeta* __restrict__ meta, const int2* __restrict__ ranges, int nr,
+                                 const double* __restrict__ vals, const int* __restrict__ structs,
+                                 const double* __restrict__ y, double* x) {
+  __shared__ double sh[kSmallK];
+  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
+    const int2 rg = ranges[r];
+    for (int s = rg.y; s >= rg.x; --s) bwd_one(meta[s], vals, structs, y, x, sh);
+  }
+}
+
+
+// ---- one-launch supernodal triangular solve (forward then backward) with
+// dynamic task fetch.  Tasks are stored in dependency order: for each height
+// (ascending) the forward diagonal rows (F1) then the off-diagonal rows (F2);
+// then for each height (descending) the backward off-diagonal rows (B1) then
+// the diagonal rows (B2).  A warp takes the next task from a global counter,
+// so every task it may wait on was taken earlier by a running warp: the waits
+// always end.  Waits are bounded anyway: on exhaustion the kernel raises
+// err[0] and returns (the host reports CC_ERR_TIMEOUT).
+struct PTask {
+  long long moff;
+  int ncols;
+  int xoff;
+  int out;
+  int kind;  // 0 F1, 1 F2, 2 B1, 3 B2
+  int sn;    // supernode
+  int gate;  // F1/B1: index into the gate thresholds; F2/B2: number of rows of the supernode
+  int k;     // rows of the supernode (B1 also waits for the supernode's whole forward step)
+};
+
+__device__ __forceinline__ bool wait_geq(const unsigned int* p, unsigned int v, unsigned int* err) {
+  long long spins = 0;
+  while (*(volatile const unsigned int*)p < v) {
+    if (*(volatile unsigned int*)err) return false;
+    if (++spins > (1ll << 24)) {
+      atomicExch(err, 1u);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_lu_persistent(const PTask* __restrict__ tasks, int ntasks,
+                                                       const double* __restrict__ vals, const int* __restrict__ structs,
+                                                       const int* __restrict__ pivrow, double* b, double* y, double* t,
+                                                       double* x, unsigned int* ctr /* [0] next task, [1] F2 done,
+                                                       [2] B2 done, then per supernode: F1 rows done, B1 rows done */,
+                                                       const unsigned int* __restrict__ gates, int nsuper,
+                                                       unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  unsigned int* f1done = ctr + 4;
+  unsigned int* b1done = ctr + 4 + nsuper;
+  while (true) {
+    int ti = 0;
+    if (lane == 0) ti = (int)atomicAdd(ctr, 1u);
+    ti = __shfl_sync(0xffffffffu, ti, 0);
+    if (ti >= ntasks) return;
+    const PTask tk = tasks[ti];
+    bool ok = true;
+    if (lane == 0) {
+      if (tk.kind == 0) ok = wait_geq(ctr + 1, gates[tk.gate], err);        // all F2 of lower heights
+      else if (tk.kind == 1) ok = wait_geq(f1done + tk.sn, tk.gate, err);  // y_s complete
+      else if (tk.kind == 2)  // all B2 of higher heights, and y_s complete
+        ok = wait_geq(ctr + 2, gates[tk.gate], err) && wait_geq(f1done + tk.sn, tk.k, err);
+      else ok = wait_geq(b1done + tk.sn, tk.gate, err);                    // t_s complete
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) return;
+    __threadfence();
+    const double* __restrict__ row = vals + tk.moff;
+    double a = 0.0;
+    if (tk.kind == 0) {
+      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(b + pivrow[tk.xoff + c]);
+    } else if (tk.kind == 1) {
+      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(y + tk.xoff + c);
+    } else if (tk.kind == 2) {
+      const int* __restrict__ g = structs + tk.xoff;
+      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(x + g[c]);
+    } else {
+      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(t + tk.xoff + c);
+    }
+    a = warp_sum(a);
+    if (lane == 0) {
+      if (tk.kind == 0) {
+        y[tk.out] = a;
+        __threadfence();
+        atomicAdd(f1done + tk.sn, 1u);
+      } else if (tk.kind == 1) {
+        atomicAdd(b + tk.out, -a);
+        __threadfence();
+        atomicAdd(ctr + 1, 1u);
+      } else if (tk.kind == 2) {
+        t[tk.out] = __ldcg(y + tk.out) - a;
+        __threadfence();
+        atomicAdd(b1done + tk.sn, 1u);
+      } else {
+        x[tk.out] = a;
+        __threadfence();
+        atomicAdd(ctr + 2, 1u);
+      }
+    }
+  }
+}
+
 __global__ void k_axpy(double* __restrict__ phi, const double* __restrict__ e, long long N) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     phi[i] += e[i];
@@ -240,30 +418,64 @@ __global__ void k_norm2(const double* __restrict__ v, long long N, double* __res
   if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
 }
 
+// ---- Krylov helpers (GMRES with the V-cycle as right preconditioner)
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, long long N, double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// w -= (*h) v
+__global__ void k_axpy_dev(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ h,
+                           long long N) {
+  const double a = *h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    w[i] -= a * v[i];
+}
+
+// out = sign * in / sqrt(*nrm2)
+__global__ void k_scale_norm(double* __restrict__ out, const double* __restrict__ in, const double* __restrict__ nrm2,
+                             double sign, long long N) {
+  const double a = sign / sqrt(*nrm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * in[i];
+}
+
+// u = sum_i y_i V_i  (y in device memory, V_i at base + i*N)
+__global__ void k_combine(double* __restrict__ u, const double* __restrict__ V, const double* __restrict__ y, int k,
+                          long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int j = 0; j < k; ++j) a += y[j] * V[(long long)j * N + i];
+    u[i] = a;
+  }
+}
+
 // r = f for unknowns (0 elsewhere), minus the ghost terms of phi1 rows next to the box.
 __global__ void k_rhs_base(const double* __restrict__ f, const double* __restrict__ gbox, double* __restrict__ r,
                            const uint8_t* __restrict__ typ, StencilP P) {
   const int n = P.n;
-  const long long N = (long long)n * n * n;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const uint8_t t = typ[idx];
-    double v = t ? f[idx] : 0.0;
-    if (t == 1) {
-      const int c[3] = {(int)(idx / ((long long)n * n)), (int)((idx / n) % n), (int)(idx % n)};
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const long long idx = ((long long)i * n + j) * n + k;
+  const uint8_t t = typ[idx];
+  double v = t ? f[idx] : 0.0;
+  if (t == 1) {
+    const int c[3] = {i, j, k};
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int cl = pos_class(c[d], n);
-        if (cl == 2) continue;
-        const int side = cl >= 3 ? 1 : 0;
-        const int t0 = d == 0 ? c[1] : c[0];
-        const int t1 = d == 2 ? c[1] : c[2];
-        const double gv = gbox[((long long)(2 * d + side) * n + t0) * n + t1];
-        v -= P.g[d][cl] * P.inv12h2 * gv;
-      }
+    for (int d = 0; d < 3; ++d) {
+      const int cl = pos_class(c[d], n);
+      if (cl == 2) continue;
+      const int side = cl >= 3 ? 1 : 0;
+      const int t0 = d == 0 ? c[1] : c[0];
+      const int t1 = d == 2 ? c[1] : c[2];
+      const double gv = gbox[((long long)(2 * d + side) * n + t0) * n + t1];
+      v -= P.g[d][cl] * P.inv12h2 * gv;
     }
-    r[idx] = v;
   }
+  r[idx] = v;
 }
 
 // owners of merged cells: r[o] = sum_p w_p f[p]   (volume-weighted mean, Sec. 4.2)
@@ -316,6 +528,19 @@ struct DevLU {
   double* rval = nullptr;
   long long entries = 0;
   long long rnnz = 0;
+  // fused small-supernode schedule
+  SnMeta* meta = nullptr;
+  int2* ranges = nullptr;
+  int nranges = 0;
+  int hcut = -1;                      // heights <= hcut run in the subtree kernels
+  double bytes_subtree = 0;           // algorithmic bytes of one subtree launch (fwd or bwd)
+  // one-launch schedule
+  PTask* ptasks = nullptr;
+  int nptasks = 0;
+  unsigned int* pgates = nullptr;
+  unsigned int* pctr = nullptr;       // 4 + 2 nsuper counters
+  int nsuper = 0;
+  double pbytes = 0;
   long long task_bytes[4] = {0, 0, 0, 0};  // algorithmic bytes per solve phase (matrix + vectors)
 };
 
@@ -330,7 +555,17 @@ struct DevLevel {
   long long p2_nnz = 0;
   DevLU lu;
   double *s = nullptr, *e = nullptr, *tmp = nullptr;
+  float *s32 = nullptr, *e32 = nullptr, *tmp32 = nullptr;  // mixed precision V-cycle
+  template <class T> T* bs();
+  template <class T> T* be();
+  template <class T> T* btmp();
 };
+template <> double* DevLevel::bs<double>() { return s; }
+template <> double* DevLevel::be<double>() { return e; }
+template <> double* DevLevel::btmp<double>() { return tmp; }
+template <> float* DevLevel::bs<float>() { return s32; }
+template <> float* DevLevel::be<float>() { return e32; }
+template <> float* DevLevel::btmp<float>() { return tmp32; }
 
 enum Prof {
   P_JACOBI,
@@ -347,11 +582,14 @@ enum Prof {
   P_AXPY,
   P_NORM,
   P_RHS,
+  P_SUBTREE,
+  P_PERSIST,
   P_COUNT
 };
 const char* kProfNames[P_COUNT] = {"jacobi",      "resid_phi1", "resid_phi2", "restrict", "prolong",
                                    "lu_rhs",      "trsv_fwd_diag", "trsv_fwd_update", "trsv_bwd_update",
-                                   "trsv_bwd_diag", "lu_scatter", "axpy", "norm", "rhs"};
+                                   "trsv_bwd_diag", "lu_scatter", "axpy", "norm", "rhs",
+                                   "lu_subtree", "lu_persistent"};
 
 }  // namespace
 
@@ -368,6 +606,7 @@ struct cc_solver {
   // finest level extras
   double *r = nullptr, *phi = nullptr, *s0 = nullptr, *f = nullptr, *gbox = nullptr, *gpatch = nullptr;
   double* norm = nullptr;   // device scalar
+  unsigned int* err_flag = nullptr;  // raised by a bounded wait that ran out
   double* hnorm = nullptr;  // pinned host scalar
   int ngroups = 0;
   int *g_owner = nullptr, *g_ptr = nullptr, *g_part = nullptr;
@@ -381,6 +620,13 @@ struct cc_solver {
   cc_info info;
   // graphs
   cudaGraphExec_t cycle_exec = nullptr;
+  // Krylov workspace (allocated on first use)
+  double* kV = nullptr;     // (m+1) grid vectors
+  double* kw = nullptr;     // work vector
+  double* kdots = nullptr;  // device scalars
+  double* khdots = nullptr; // pinned copy
+  double* kzero = nullptr;  // a zero grid array
+  int km = 0;
   // profiling
   bool prof = false;
   long long prof_launch[P_COUNT];
@@ -421,6 +667,10 @@ cc_status dupload(cc_solver* S, T** p, const std::vector<T>& v) {
   if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return CC_OK;
 }
+
+// 3-D launch over an n^3 grid: threads along k
+dim3 grid3(int n, int block) { return dim3((n + block - 1) / block, n, n); }
+int block3(int n) { return n >= 128 ? 128 : (n >= 64 ? 64 : 32); }
 
 int grid_for(const cc_solver* S, long long work, int block) {
   long long b = (work + block - 1) / block;
@@ -466,7 +716,7 @@ void prof_flush(cc_solver* S) {
   S->pending.clear();
 }
 
-StencilP make_stencil(const Level& L) {
+StencilP make_stencil(const Level& L, double omega) {
   StencilP P;
   P.n = L.n;
   P.inv12h2 = 1.0 / (12.0 * L.h * L.h);
@@ -477,6 +727,12 @@ StencilP make_stencil(const Level& L) {
       P.g[d][c] = r.g[c];
     }
   }
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b)
+      for (int cc = 0; cc < 5; ++cc) {
+        const double dg = (P.c[0][a][3] + P.c[1][b][3] + P.c[2][cc][3]) * P.inv12h2;
+        P.winv[a][b][cc] = omega / dg;
+      }
   return P;
 }
 
@@ -538,7 +794,53 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   std::vector<Task> per[4];
   std::vector<std::vector<Task>> byh[4];
   for (int ph = 0; ph < 4; ++ph) byh[ph].assign(F.height + 1, {});
+  // small supernodes run fused (subtree kernel below hcut, per-height kernels above)
+  std::vector<SnMeta> meta(F.nsuper);
+  std::vector<int> lo(F.nsuper);
+  std::vector<char> small(F.nsuper);
+  std::vector<int> parent(F.nsuper, -1);
   for (int s = 0; s < F.nsuper; ++s) {
+    const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+    const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+    meta[s] = {F.off_linv[s], F.off_uinv[s], F.off_l21[s], F.off_u12[s], F.sn_struct[s], f0, k, m, 0};
+    small[s] = k <= kSmallK;
+    lo[s] = s;
+  }
+  // postorder numbering: the subtree of s is the contiguous range [lo[s], s]
+  for (int s = 0; s < F.nsuper; ++s) {
+    parent[s] = F.sn_parent[s];
+    if (parent[s] >= 0) lo[parent[s]] = std::min(lo[parent[s]], lo[s]);
+  }
+  // hcut: the largest height such that every supernode at or below it is small
+  // and the subtrees rooted there still number at least 8 per SM
+  std::vector<int> allsmall(F.height + 1, 1);
+  for (int s = 0; s < F.nsuper; ++s)
+    if (!small[s]) allsmall[F.sn_height[s]] = 0;
+  D.hcut = -1;
+  for (int h = 0; h <= F.height; ++h) {
+    if (!allsmall[h]) break;
+    int roots = 0;
+    for (int s = 0; s < F.nsuper; ++s)
+      if (F.sn_height[s] <= h && (parent[s] < 0 || F.sn_height[parent[s]] > h)) ++roots;
+    if (h > 0 && roots < 8 * S->nsm) break;
+    D.hcut = h;
+  }
+  auto sn_bytes = [&](int s, bool fwd) {
+    const SnMeta& q = meta[s];
+    double b = fwd ? 8.0 * q.k * (q.k + 1) / 2 + 8.0 * (double)q.m * q.k : 8.0 * q.k * (q.k + 1) / 2 + 8.0 * (double)q.m * q.k;
+    return b + 12.0 * q.k + 12.0 * q.m;
+  };
+  std::vector<int2> ranges;
+  D.bytes_subtree = 0;
+  for (int s = 0; s < F.nsuper; ++s) {
+    if (F.sn_height[s] <= D.hcut) D.bytes_subtree += sn_bytes(s, true);
+    if (F.sn_height[s] <= D.hcut && (parent[s] < 0 || F.sn_height[parent[s]] > D.hcut)) ranges.push_back(make_int2(lo[s], s));
+  }
+  D.nranges = (int)ranges.size();
+  if ((st = dupload(S, &D.meta, meta))) return st;
+  if ((st = dupload(S, &D.ranges, ranges))) return st;
+  for (int s = 0; s < F.nsuper; ++s) {
+    if (F.sn_height[s] <= D.hcut) continue;  // handled by the subtree kernels
     const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
     const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
     const int hgt = F.sn_height[s];
@@ -571,6 +873,61 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
     D.task_bytes[ph] = bytes;
   }
   if ((st = dupload(S, &D.tasks, all))) return st;
+  {
+    // one-launch schedule over every supernode (no subtree split)
+    std::vector<PTask> pt;
+    std::vector<unsigned int> gates;
+    std::vector<std::vector<int>> by_h(F.height + 1);
+    for (int s = 0; s < F.nsuper; ++s) by_h[F.sn_height[s]].push_back(s);
+    unsigned int f2_count = 0;
+    D.pbytes = 0;
+    for (int h = 0; h <= F.height; ++h) {
+      gates.push_back(f2_count);  // F1 at height h waits for all F2 below
+      const int g = (int)gates.size() - 1;
+      for (int s : by_h[h]) {
+        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+        for (int r = 0; r < k; ++r) {
+          pt.push_back({F.off_linv[s] + (long long)r * k, r + 1, f0, f0 + r, 0, s, g, k});
+          D.pbytes += 12.0 * (r + 1) + 8;
+        }
+      }
+      for (int s : by_h[h]) {
+        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+        const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+        for (int a = 0; a < m; ++a) {
+          pt.push_back({F.off_l21[s] + (long long)a * k, k, f0, F.structs[F.sn_struct[s] + a], 1, s, k, k});
+          ++f2_count;
+          D.pbytes += 8.0 * k + 12;
+        }
+      }
+    }
+    unsigned int b2_count = 0;
+    for (int h = F.height; h >= 0; --h) {
+      gates.push_back(b2_count);  // B1 at height h waits for all B2 above
+      const int g = (int)gates.size() - 1;
+      for (int s : by_h[h]) {
+        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+        const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+        for (int r = 0; r < k; ++r) {
+          pt.push_back({F.off_u12[s] + (long long)r * m, m, (int)F.sn_struct[s], f0 + r, 2, s, g, k});
+          D.pbytes += 12.0 * m + 16;
+        }
+      }
+      for (int s : by_h[h]) {
+        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
+        for (int r = 0; r < k; ++r) {
+          pt.push_back({F.off_uinv[s] + (long long)r * k + r, k - r, f0 + r, f0 + r, 3, s, k, k});
+          ++b2_count;
+          D.pbytes += 8.0 * (k - r) + 8;
+        }
+      }
+    }
+    D.nptasks = (int)pt.size();
+    D.nsuper = F.nsuper;
+    if ((st = dupload(S, &D.ptasks, pt))) return st;
+    if ((st = dupload(S, &D.pgates, gates))) return st;
+    if ((st = dalloc(S, &D.pctr, 4 + 2 * (size_t)F.nsuper))) return st;
+  }
   if ((st = dalloc(S, &D.b, F.n))) return st;
   if ((st = dalloc(S, &D.y, F.n))) return st;
   if ((st = dalloc(S, &D.t, F.n))) return st;
@@ -615,36 +972,56 @@ void launch_tasks(cc_solver* S, DevLU& D, int ph, int h) {
 }
 
 // phi[cells] = A^{-1} (s[cells] - R phi) with the stored factors
-void lu_solve(cc_solver* S, DevLU& D, const double* s, double* phi) {
+template <class T>
+void lu_solve(cc_solver* S, DevLU& D, const T* s, T* phi) {
   if (D.np == 0) return;
   const int block = 256;
   {
-    ProfScope ps(S, P_LURHS, 8.0 * D.np + 12.0 * D.rnnz + 16.0 * D.np);
-    k_lu_rhs<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.np, D.cell, D.rptr, D.rcol, D.rval, s, phi);
+    ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 8.0 * D.np);
+    k_lu_rhs<T><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.np, D.cell, D.rptr, D.rcol, D.rval, s, phi);
   }
-  for (int h = 0; h <= D.height; ++h) {
+  if (S->prm.lu_persistent) {
+    cudaMemsetAsync(D.pctr, 0, sizeof(unsigned int) * (4 + 2 * (size_t)D.nsuper), S->stream);
+    ProfScope ps(S, P_PERSIST, D.pbytes);
+    k_lu_persistent<<<S->nsm * 8, 256, 0, S->stream>>>(D.ptasks, D.nptasks, D.vals, D.structs, D.pivrow, D.b, D.y,
+                                                       D.t, D.x, D.pctr, D.pgates, D.nsuper, S->err_flag);
+  } else {
+  if (D.nranges > 0) {
+    ProfScope ps(S, P_SUBTREE, D.bytes_subtree);
+    k_lu_subtree_fwd<<<std::min(D.nranges, S->nsm * 8), 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals,
+                                                                               D.structs, D.pivrow, D.b, D.y);
+  }
+  for (int h = D.hcut + 1; h <= D.height; ++h) {
     launch_tasks(S, D, T_F1, h);
     launch_tasks(S, D, T_F2, h);
   }
-  for (int h = D.height; h >= 0; --h) {
+  for (int h = D.height; h > D.hcut; --h) {
     launch_tasks(S, D, T_B1, h);
     launch_tasks(S, D, T_B2, h);
   }
-  ProfScope ps(S, P_SCATTER, 16.0 * D.np);
-  k_scatter<<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
+  if (D.nranges > 0) {
+    ProfScope ps(S, P_SUBTREE, D.bytes_subtree);
+    k_lu_subtree_bwd<<<std::min(D.nranges, S->nsm * 8), 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals,
+                                                                               D.structs, D.y, D.x);
+  }
+  }
+  ProfScope ps(S, P_SCATTER, (8.0 + 4.0 + sizeof(T)) * D.np);
+  k_scatter<T><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
 }
 
-void jacobi(cc_solver* S, DevLevel& L, const double* in, const double* s, double* out) {
+template <class T>
+void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
   const int block = 256;
-  ProfScope ps(S, P_JACOBI, 25.0 * L.N);
-  k_jacobi<<<grid_for(S, L.N, block), block, 0, S->stream>>>(in, s, out, L.typ, L.P, S->prm.omega);
+  ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
+  (void)block;
+  k_jacobi<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(in, s, out, L.typ, L.P);
 }
 
 void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {
   const int block = 256;
   {
     ProfScope ps(S, P_RESID1, 25.0 * L.N);
-    k_resid1<<<grid_for(S, L.N, block), block, 0, S->stream>>>(phi, s, out, L.typ, L.P, norm2);
+    k_resid1<<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(phi, s, out, L.typ, L.P, norm2);
   }
   if (phi2 && L.n2 > 0) {
     ProfScope ps(S, P_RESID2, 12.0 * L.p2_nnz);
@@ -653,44 +1030,63 @@ void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double
   }
 }
 
-void restrict_resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* coarse) {
+template <class T>
+void restrict_resid(cc_solver* S, DevLevel& L, const T* phi, const T* s, T* coarse) {
   const int block = 256;
-  ProfScope ps(S, P_RESTRICT, 17.0 * L.N);
-  k_restrict<<<grid_for(S, L.N / 8, block), block, 0, S->stream>>>(phi, s, coarse, L.typ, L.P);
+  ProfScope ps(S, P_RESTRICT, (2.0 * sizeof(T) + 1.0 + sizeof(T) / 8.0) * L.N);
+  (void)block;
+  k_restrict<T><<<grid3(L.n / 2, block3(L.n / 2)), block3(L.n / 2), 0, S->stream>>>(phi, s, coarse, L.typ, L.P);
 }
 
-void prolong(cc_solver* S, int m, const double* coarse, double* phi) {
+template <class T>
+void prolong(cc_solver* S, int m, const T* coarse, T* phi) {
   DevLevel& L = S->lev[m];
   const int block = 256;
-  ProfScope ps(S, P_PROLONG, 17.25 * L.N);
-  k_prolong<<<grid_for(S, L.N, block), block, 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
+  ProfScope ps(S, P_PROLONG, (2.0 * sizeof(T) + 1.0 + (sizeof(T) + 1.0) / 8.0) * L.N);
+  (void)block;
+  k_prolong<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
 }
 
-void vcycle_rec(cc_solver* S, int m, const double* s, double* e) {
+template <class T>
+void vcycle_rec(cc_solver* S, int m, const T* s, T* e) {
   DevLevel& L = S->lev[m];
   const int M = (int)S->lev.size() - 1;
-  cudaMemsetAsync(e, 0, L.N * sizeof(double), S->stream);
+  cudaMemsetAsync(e, 0, L.N * sizeof(T), S->stream);
   if (m == M) {
-    lu_solve(S, L.lu, s, e);
+    lu_solve<T>(S, L.lu, s, e);
     return;
   }
-  double* cur = e;
-  double* oth = L.tmp;
+  T* cur = e;
+  T* oth = L.btmp<T>();
   for (int it = 0; it < S->prm.nu1; ++it) {
-    jacobi(S, L, cur, s, oth);
+    jacobi<T>(S, L, cur, s, oth);
     std::swap(cur, oth);
-    lu_solve(S, L.lu, s, cur);
+    lu_solve<T>(S, L.lu, s, cur);
   }
-  DevLevel& C = S->lev[m + 1];
-  restrict_resid(S, L, cur, s, C.s);
-  vcycle_rec(S, m + 1, C.s, C.e);
-  prolong(S, m, C.e, cur);
+  DevLevel& Cl = S->lev[m + 1];
+  restrict_resid<T>(S, L, cur, s, Cl.bs<T>());
+  vcycle_rec<T>(S, m + 1, Cl.bs<T>(), Cl.be<T>());
+  prolong<T>(S, m, Cl.be<T>(), cur);
   for (int it = 0; it < S->prm.nu2; ++it) {
-    jacobi(S, L, cur, s, oth);
+    jacobi<T>(S, L, cur, s, oth);
     std::swap(cur, oth);
-    lu_solve(S, L.lu, s, cur);
+    lu_solve<T>(S, L.lu, s, cur);
   }
-  if (cur != e) cudaMemcpyAsync(e, cur, L.N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream);
+  if (cur != e) cudaMemcpyAsync(e, cur, L.N * sizeof(T), cudaMemcpyDeviceToDevice, S->stream);
+}
+
+// e (FP64, level 0) = VCycle(s) in the solver's precision: FP64, or FP32 for the
+// grid work with the FP64 LU-corrections (mixed precision)
+void precond(cc_solver* S, const double* s, double* e) {
+  DevLevel& L = S->lev[0];
+  if (S->prm.precision == 1) {
+    k_to_float<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(L.s32, s, L.N);
+    vcycle_rec<float>(S, 0, L.s32, L.e32);
+    cudaMemsetAsync(e, 0, L.N * sizeof(double), S->stream);
+    k_axpy_f<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(e, L.e32, L.N);
+  } else {
+    vcycle_rec<double>(S, 0, s, e);
+  }
 }
 
 // s0 = r - L phi (all rows) and ||s0||^2 into S->norm
@@ -703,7 +1099,7 @@ void outer_residual(cc_solver* S) {
 
 void one_cycle(cc_solver* S) {
   DevLevel& L = S->lev[0];
-  vcycle_rec(S, 0, S->s0, L.e);
+  precond(S, S->s0, L.e);
   {
     ProfScope ps(S, P_AXPY, 24.0 * L.N);
     k_axpy<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.e, L.N);
@@ -736,6 +1132,15 @@ std::vector<int> finish_host_info(cc_solver* S) {
   return patch_of;
 }
 
+// Reads and clears the flag raised by a bounded wait that ran out.
+bool take_timeout(cc_solver* S) {
+  unsigned int h = 0;
+  cudaMemcpyAsync(&h, S->err_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->stream);
+  cudaStreamSynchronize(S->stream);
+  if (h) cudaMemsetAsync(S->err_flag, 0, sizeof(unsigned int), S->stream);
+  return h != 0;
+}
+
 cc_status fail(cc_solver* S, cc_status st, const std::string& msg) {
   S->err = msg;
   return st;
@@ -765,7 +1170,7 @@ cc_status build_rhs(cc_solver* S, const double* f, const double* gbox, const dou
   if (S->info.n_patches > 0)
     CK(cudaMemcpyAsync(S->gpatch, gpatch, (size_t)S->info.n_patches * sizeof(double), k, S->stream));
   ProfScope ps(S, P_RHS, 0.0);
-  k_rhs_base<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->f, S->gbox, S->r, L.typ, L.P);
+  k_rhs_base<<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(S->f, S->gbox, S->r, L.typ, L.P);
   if (S->ngroups)
     k_merge_f<<<grid_for(S, S->ngroups, 128), 128, 0, S->stream>>>(S->ngroups, S->g_owner, S->g_ptr, S->g_part,
                                                                     S->g_w, S->f, S->r);
@@ -845,7 +1250,142 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter";
   if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (take_timeout(S)) {
+    S->err = "a bounded wait in the LU solve ran out";
+    return CC_ERR_TIMEOUT;
+  }
   return result;
+}
+
+// Restarted GMRES(m), right-preconditioned by one V-cycle, on the finest level's
+// grid vectors (an acceleration of Alg. Multigrid; the V-cycle is unchanged).
+cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
+  DevLevel& L = S->lev[0];
+  const long long N = L.N;
+  const int m = std::max(2, std::min(64, S->prm.krylov_restart));
+  const int block = 256;
+  const int grid = grid_for(S, N, block);
+  if (S->km != m) {
+    cc_status st;
+    if ((st = dalloc(S, &S->kV, (size_t)(m + 1) * N))) return st;
+    if ((st = dalloc(S, &S->kw, N))) return st;
+    if ((st = dalloc(S, &S->kzero, N))) return st;
+    if ((st = dalloc(S, &S->kdots, (size_t)2 * (m + 2)))) return st;
+    if (!S->khdots) CK(cudaMallocHost((void**)&S->khdots, sizeof(double) * 2 * 66));
+    CK(cudaMemset(S->kzero, 0, N * sizeof(double)));
+    S->km = m;
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, S->stream));
+  CK(cudaMemsetAsync(S->norm, 0, sizeof(double), S->stream));
+  k_norm2<<<grid, block, 0, S->stream>>>(S->r, N, S->norm);
+  CK(cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  const double rn = std::sqrt(*S->hnorm);
+  cc_status result = CC_ERR_NOT_CONVERGED;
+  int cycles = 0, hist_n = 0;
+  double rel = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double* V = S->kV;
+  while (true) {
+    outer_residual(S);  // s0 = r - L phi, ||s0||^2 -> hnorm
+    CK(cudaStreamSynchronize(S->stream));
+    const double beta = std::sqrt(*S->hnorm);
+    rel = rn > 0 ? beta / rn : 0.0;
+    if (stats && hist_n < 256) stats->resid_hist[hist_n++] = rel;
+    if (!std::isfinite(rel)) {
+      result = CC_ERR_DIVERGED;
+      break;
+    }
+    if (rel < S->prm.rel_tol) {
+      result = CC_OK;
+      break;
+    }
+    if (cycles >= S->prm.max_iter) break;
+    k_scale_norm<<<grid, block, 0, S->stream>>>(V, S->s0, S->norm, 1.0, N);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && cycles < S->prm.max_iter; ++j) {
+      double* vj = V + (long long)j * N;
+      precond(S, vj, L.e);  // z = M v_j
+      ++cycles;
+      // w = A z = -(0 - A z)
+      resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
+      CK(cudaMemsetAsync(S->kdots, 0, sizeof(double) * (m + 2), S->stream));
+      for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
+        k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);
+        k_axpy_dev<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, S->kdots + i, N);
+      }
+      k_dot<<<grid, block, 0, S->stream>>>(S->kw, S->kw, N, S->kdots + j + 1);
+      k_scale_norm<<<grid, block, 0, S->stream>>>(V + (long long)(j + 1) * N, S->kw, S->kdots + j + 1, -1.0, N);
+      CK(cudaMemcpyAsync(S->khdots, S->kdots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, S->stream));
+      CK(cudaStreamSynchronize(S->stream));
+      // column j of H (the dots were taken with -w = -A z)
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = -S->khdots[i];
+      double hnext = std::sqrt(std::max(0.0, S->khdots[j + 1]));
+      for (int i = 0; i < j; ++i) {  // apply previous rotations
+        double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      double a = H[(size_t)j * m + j], b = hnext;
+      double r = std::hypot(a, b);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? b / r : 0.0;
+      H[(size_t)j * m + j] = r;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      double est = std::fabs(g[j + 1]) / rn;
+      if (stats && hist_n < 256) stats->resid_hist[hist_n++] = est;
+      if (!std::isfinite(est)) break;
+      if (est < 0.5 * S->prm.rel_tol || hnext == 0.0) break;
+    }
+    // y = H^{-1} g, phi += M (V y)
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int t = i + 1; t < k; ++t) s -= H[(size_t)i * m + t] * y[t];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(S->kdots + m + 2, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, S->stream));
+    k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
+    precond(S, S->kw, L.e);
+    ++cycles;
+    k_axpy<<<grid, block, 0, S->stream>>>(S->phi, L.e, N);
+  }
+  if (S->nabs) k_absorbed<<<grid_for(S, S->nabs, 128), 128, 0, S->stream>>>(S->phi, S->nabs, S->a_cell, S->a_own);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, S->stream));
+  if (phi_out)
+    CK(cudaMemcpyAsync(phi_out, S->phi, N * sizeof(double),
+                       where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (S->prof) prof_flush(S);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = cycles;
+    stats->converged = result == CC_OK;
+    stats->rel_resid = rel;
+    stats->ms_solve = ms;
+  }
+  if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter V-cycles";
+  if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (take_timeout(S)) {
+    S->err = "a bounded wait in the LU solve ran out";
+    return CC_ERR_TIMEOUT;
+  }
+  return result;
+}
+
+cc_status run_solve(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return S->prm.krylov ? gmres_loop(S, phi_out, where, stats) : solve_loop(S, phi_out, where, stats);
 }
 
 }  // namespace
@@ -866,6 +1406,10 @@ void cc_default_params(cc_params* p) {
   p->use_graph = 1;
   p->lu_leaf = 64;
   p->host_threads = 0;
+  p->krylov = 0;
+  p->krylov_restart = 30;
+  p->precision = 0;
+  p->lu_persistent = 1;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -900,6 +1444,7 @@ void cc_destroy(cc_solver* S) {
   drop_graph(S);
   for (void* p : S->allocs) cudaFree(p);
   if (S->hnorm) cudaFreeHost(S->hnorm);
+  if (S->khdots) cudaFreeHost(S->khdots);
   if (S->own_stream) cudaStreamDestroy(S->own_stream);
   delete S;
 }
@@ -912,7 +1457,8 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     S->prm = *p;
   else
     cc_default_params(&S->prm);
-  if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1) {
+  if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
+      S->prm.precision < 0 || S->prm.precision > 1) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }
@@ -947,7 +1493,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   std::vector<std::vector<double>> mats_val(S->host.size());
   for (int m = 0; m <= M; ++m) {
     const Level& L = S->host[m];
-    sp[m] = make_stencil(L);
+    sp[m] = make_stencil(L, S->prm.omega);
     if (m < M) {
       // L22 over compact phi2 indices; L21 rows keep grid columns for the RHS kernel
       const int n2 = (int)L.p2_cell.size();
@@ -1056,6 +1602,11 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dalloc(S, &D.s, D.N));
     TRY(dalloc(S, &D.e, D.N));
     TRY(dalloc(S, &D.tmp, D.N));
+    if (S->prm.precision == 1) {
+      TRY(dalloc(S, &D.s32, D.N));
+      TRY(dalloc(S, &D.e32, D.N));
+      TRY(dalloc(S, &D.tmp32, D.N));
+    }
     S->info.n[m] = L.n;
     S->info.n_unknowns[m] = L.n_unknowns;
     S->info.n_phi2[m] = D.n2;
@@ -1073,6 +1624,11 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dalloc(S, &S->f, D0.N));
     TRY(dalloc(S, &S->gbox, (size_t)6 * L0.n * L0.n));
     TRY(dalloc(S, &S->norm, 1));
+    TRY(dalloc(S, &S->err_flag, 1));
+    if (cudaMemset(S->err_flag, 0, sizeof(unsigned int)) != cudaSuccess) {
+      st = CC_ERR_CUDA;
+      goto failed;
+    }
     if (cudaMallocHost((void**)&S->hnorm, sizeof(double)) != cudaSuccess) {
       st = CC_ERR_OOM;
       goto failed;
@@ -1262,7 +1818,7 @@ cc_status cc_solve(cc_solver* S, const double* f, const double* g_box, const dou
   CK(cudaMemcpyAsync(S->phi, phi, L.N * sizeof(double),
                      where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
   k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
-  return solve_loop(S, phi, where, stats);
+  return run_solve(S, phi, where, stats);
 }
 
 cc_status cc_solve_r(cc_solver* S, const double* r, double* phi, int where, cc_stats* stats) {
@@ -1274,7 +1830,7 @@ cc_status cc_solve_r(cc_solver* S, const double* r, double* phi, int where, cc_s
   CK(cudaMemcpyAsync(S->phi, phi, L.N * sizeof(double), k, S->stream));
   k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->r, L.typ, L.N);
   k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
-  return solve_loop(S, phi, where, stats);
+  return run_solve(S, phi, where, stats);
 }
 
 cc_status cc_residual(cc_solver* S, int level, const double* phi, const double* rhs, double* out, int phi2_rows) {
@@ -1292,7 +1848,7 @@ cc_status cc_jacobi(cc_solver* S, int level, const double* phi_in, const double*
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   cc_status st = check_level(S, level);
   if (st) return st;
-  jacobi(S, S->lev[level], phi_in, rhs, phi_out);
+  jacobi<double>(S, S->lev[level], phi_in, rhs, phi_out);
   CK(cudaGetLastError());
   return CC_OK;
 }
@@ -1303,8 +1859,9 @@ cc_status cc_lu_correction(cc_solver* S, int level, double* phi, const double* r
   cc_status st = check_level(S, level);
   if (st) return st;
   if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
-  lu_solve(S, S->lev[level].lu, rhs, phi);
+  lu_solve<double>(S, S->lev[level].lu, rhs, phi);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 
@@ -1314,7 +1871,7 @@ cc_status cc_restrict_residual(cc_solver* S, int level, const double* phi, const
   cc_status st = check_level(S, level);
   if (st) return st;
   if (level + 1 >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "no coarser level");
-  restrict_resid(S, S->lev[level], phi, rhs, coarse);
+  restrict_resid<double>(S, S->lev[level], phi, rhs, coarse);
   CK(cudaGetLastError());
   return CC_OK;
 }
@@ -1325,7 +1882,7 @@ cc_status cc_prolong_add(cc_solver* S, int level, const double* coarse, double* 
   cc_status st = check_level(S, level);
   if (st) return st;
   if (level + 1 >= (int)S->lev.size()) return fail(S, CC_ERR_INVALID_ARG, "no coarser level");
-  prolong(S, level, coarse, phi);
+  prolong<double>(S, level, coarse, phi);
   CK(cudaGetLastError());
   return CC_OK;
 }
@@ -1335,16 +1892,18 @@ cc_status cc_bottom_solve(cc_solver* S, const double* rhs, double* phi) {
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   DevLevel& L = S->lev.back();
   CK(cudaMemsetAsync(phi, 0, L.N * sizeof(double), S->stream));
-  lu_solve(S, L.lu, rhs, phi);
+  lu_solve<double>(S, L.lu, rhs, phi);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 
 cc_status cc_vcycle(cc_solver* S, const double* rhs, double* e) {
   if (!S || !rhs || !e) return CC_ERR_INVALID_ARG;
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
-  vcycle_rec(S, 0, rhs, e);
+  precond(S, rhs, e);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 

@@ -615,6 +615,12 @@ struct LevelBuilder {
       out.bcoef.push_back(coef);
     }
     out.degree = degree;
+    // a Laplacian row must have a negative diagonal: a fit whose own-cell
+    // coefficient is not negative (slivers next to the boundary) is rejected
+    double diag = 0.0;
+    for (int i = 0; i < nc; ++i)
+      if (cells[i] == q) diag += out.vals[i];
+    if (!(diag < 0.0)) return false;
     out.ok = true;
     return true;
   }

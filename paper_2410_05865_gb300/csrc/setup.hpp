@@ -127,6 +127,7 @@ struct SuperLU {
   int nsuper = 0;
   std::vector<int> sn_first;        // first ND position of each supernode (size nsuper+1)
   std::vector<int> sn_height;       // height in the supernode tree (leaves 0)
+  std::vector<int> sn_parent;       // parent in the supernode tree (-1 for roots); subtrees are contiguous
   std::vector<long long> sn_struct; // offset into structs (size nsuper+1)
   std::vector<int> structs;         // ND positions of struct(s), ascending
   // value offsets (doubles) into vals for each supernode's blocks

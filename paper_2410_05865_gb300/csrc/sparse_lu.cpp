@@ -3,7 +3,8 @@
 //
 // Ordering: geometric nested dissection of the symmetrised graph of A (edges
 // i~j where a_ij or a_ji is non-zero): a vertex set larger than the leaf size is
-// split at the median of its longest coordinate extent; the separator is the
+// split by the axis-aligned plane (median +-2 on each axis) with the smallest
+// separator among those leaving both parts within 30-70 %; the separator is the
 // set of vertices on the upper side that touch the lower side; the two parts
 // are ordered recursively and the separator last (Alg. ND numbers separators
 // last).  Each leaf and each separator is one supernode.
@@ -59,21 +60,53 @@ struct NdBuilder {
         lo[d] = std::min(lo[d], xyz[3 * v + d]);
         hi[d] = std::max(hi[d], xyz[3 * v + d]);
       }
-    int ax = 0;
-    for (int d = 1; d < 3; ++d)
-      if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
-    if (hi[ax] == lo[ax]) {  // a single point cloud: dense leaf
+    // candidate planes: the median of every axis with extent, shifted by -2..2;
+    // keep the smallest one-sided separator whose parts stay within 30-70 %
+    int best_ax = -1, best_t = 0;
+    long long best_score = -1;
+    std::vector<int> cs;
+    cs.reserve(V.size());
+    for (int d = 0; d < 3; ++d) {
+      if (hi[d] == lo[d]) continue;
+      cs.clear();
+      for (int v : V) cs.push_back(xyz[3 * v + d]);
+      std::nth_element(cs.begin(), cs.begin() + cs.size() / 2, cs.end());
+      const int med = cs[cs.size() / 2];
+      for (int sh = -2; sh <= 2; ++sh) {
+        int t = med + sh;
+        if (t <= lo[d] || t > hi[d]) continue;
+        ++stamp_val;
+        long long na = 0;
+        for (int v : V)
+          if (xyz[3 * v + d] < t) {
+            stamp[v] = stamp_val;
+            ++na;
+          }
+        long long nc = 0;
+        for (int v : V)
+          if (xyz[3 * v + d] >= t)
+            for (int u : adj[v])
+              if (stamp[u] == stamp_val) {
+                ++nc;
+                break;
+              }
+        const long long nb = (long long)V.size() - na - nc;
+        const long long mx = std::max(na, nb);
+        long long score = nc * 4 + (mx * 10 > (long long)V.size() * 7 ? (long long)V.size() : 0);
+        if (best_score < 0 || score < best_score) {
+          best_score = score;
+          best_ax = d;
+          best_t = t;
+        }
+      }
+    }
+    if (best_ax < 0) {
       std::sort(V.begin(), V.end());
       nodes.push_back({V, {}});
       roots.push_back((int)nodes.size() - 1);
       return roots;
     }
-    std::vector<int> cs;
-    cs.reserve(V.size());
-    for (int v : V) cs.push_back(xyz[3 * v + ax]);
-    std::nth_element(cs.begin(), cs.begin() + cs.size() / 2, cs.end());
-    int t = cs[cs.size() / 2];
-    if (t == lo[ax]) t = lo[ax] + 1;  // keep the lower part non-empty
+    const int ax = best_ax, t = best_t;
     std::vector<int> A, B, C;
     for (int v : V) (xyz[3 * v + ax] < t ? A : B).push_back(v);
     ++stamp_val;
@@ -324,6 +357,7 @@ int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const st
       kids[sid[pn]].push_back(k);
     }
   }
+  out.sn_parent = sparent;
   out.sn_height.assign(ns, 0);
   for (int k = 0; k < ns; ++k)
     for (int c : kids[k]) out.sn_height[k] = std::max(out.sn_height[k], out.sn_height[c] + 1);

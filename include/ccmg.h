@@ -84,7 +84,7 @@ typedef struct {
                         restriction, prolongation) with FP64 LU-corrections, bottom
                         solve and outer residual (defect correction) (0) */
   int lu_persistent; /* 1: each triangular solve is one launch with dynamic task fetch
-                        and bounded waits; 0: one launch per tree height and phase (1) */
+                        and bounded waits; 0: one launch per tree height and phase (0) */
 } cc_params;
 
 typedef struct {

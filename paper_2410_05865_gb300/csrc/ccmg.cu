@@ -40,6 +40,16 @@ __device__ __forceinline__ int pos_class(int p, int n) {
   return p == 0 ? 0 : (p == 1 ? 1 : (p == n - 2 ? 3 : (p == n - 1 ? 4 : 2)));
 }
 
+// The interior row of eq. regularLaplaceDiscretization: (16 sum_{|o|=1} - sum_{|o|=2} - 90 c) / (12 h^2),
+// the neighbour sums taken in the order +i, -i, +j, -j, +k, -k so that every kernel rounds alike.
+template <class T>
+__device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1, T km1, T ip2, T im2, T jp2, T jm2,
+                                        T kp2, T km2, double inv12h2) {
+  const T s1 = ip1 + im1 + jp1 + jm1 + kp1 + km1;
+  const T s2 = ip2 + im2 + jp2 + jm2 + kp2 + km2;
+  return (T(16) * s1 - s2 - T(90) * c0) * T(inv12h2);
+}
+
 // (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
 template <class T>
 __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int j, int k, const StencilP& P) {
@@ -48,10 +58,9 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
   const long long idx = (long long)i * nn + (long long)j * n + k;
   const int ci = pos_class(i, n), cj = pos_class(j, n), ck = pos_class(k, n);
   if (ci == 2 && cj == 2 && ck == 2) {
-    const T c0 = phi[idx];
-    T s1 = phi[idx + nn] + phi[idx - nn] + phi[idx + n] + phi[idx - n] + phi[idx + 1] + phi[idx - 1];
-    T s2 = phi[idx + 2 * nn] + phi[idx - 2 * nn] + phi[idx + 2 * n] + phi[idx - 2 * n] + phi[idx + 2] + phi[idx - 2];
-    return (T(16) * s1 - s2 - T(90) * c0) * T(P.inv12h2);
+    return interior13<T>(phi[idx], phi[idx + nn], phi[idx - nn], phi[idx + n], phi[idx - n], phi[idx + 1],
+                         phi[idx - 1], phi[idx + 2 * nn], phi[idx - 2 * nn], phi[idx + 2 * n], phi[idx - 2 * n],
+                         phi[idx + 2], phi[idx - 2], P.inv12h2);
   }
   const int cls[3] = {ci, cj, ck};
   const long long stride[3] = {nn, (long long)n, 1};
@@ -69,22 +78,66 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
 }
 
 // Grid kernels run on a 3-D launch: threads along k, blockIdx.y = j, blockIdx.z = i.
-template <class T>
-__global__ void k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s, T* __restrict__ phi_out,
-                         const uint8_t* __restrict__ typ, StencilP P) {
+// SMO-1 with 2.5-D blocking: a BY x BX tile of (j, k) columns marches along i over
+// IC planes.  Plane i (with a 2-cell halo in j and k) is staged in shared memory,
+// the i -+ 1, 2 neighbours of each column ride in a register queue, so each value
+// is read from HBM/L2 about once instead of through 13 scattered loads.  Cells
+// whose row is not the interior row (near the box) take apply_regular.
+template <class T, int BX, int BY, int IC>
+__global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ phi_in, const T* __restrict__ s,
+                                                           T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
+                                                           StencilP P) {
+  __shared__ T tile[BY + 4][BX + 4];
   const int n = P.n;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= n) return;
-  const long long idx = ((long long)i * n + j) * n + k;
-  const T v = phi_in[idx];
-  if (typ[idx] == 1) {
-    const T lphi = apply_regular<T>(phi_in, i, j, k, P);
-    // omega / D from the class table: one multiply instead of a divide
-    phi_out[idx] = fma(T(P.winv[pos_class(i, n)][pos_class(j, n)][pos_class(k, n)]), s[idx] - lphi, v);
-  } else {
-    phi_out[idx] = v;
+  const long long nn = (long long)n * n;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int k0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+  const int k = k0 + tx, j = j0 + ty;
+  const int i0 = blockIdx.z * IC;
+  const int i1 = min(i0 + IC, n);
+  const bool inb = k < n && j < n;
+  const long long col = (long long)j * n + k;
+  // q[t] = phi(i - 2 + t) of this column; q[2] is also in the tile
+  T q[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int ii = i0 - 2 + t;
+    q[t] = (inb && ii >= 0 && ii < n) ? phi_in[(long long)ii * nn + col] : T(0);
+  }
+  const int cj = pos_class(j, n), ck = pos_class(k, n);
+  for (int i = i0; i < i1; ++i) {
+    __syncthreads();
+    for (int e = tid; e < (BY + 4) * (BX + 4); e += BX * BY) {
+      const int ly = e / (BX + 4), lx = e - ly * (BX + 4);
+      const int jj = j0 + ly - 2, kk = k0 + lx - 2;
+      tile[ly][lx] = (jj >= 0 && jj < n && kk >= 0 && kk < n) ? phi_in[(long long)i * nn + (long long)jj * n + kk]
+                                                              : T(0);
+    }
+    __syncthreads();
+    if (inb) {
+      const long long idx = (long long)i * nn + col;
+      const T v = q[2];
+      T res = v;
+      if (typ[idx] == 1) {
+        const int ci = pos_class(i, n);
+        T lphi;
+        if (ci == 2 && cj == 2 && ck == 2) {
+          const int y = ty + 2, x = tx + 2;
+          lphi = interior13<T>(v, q[3], q[1], tile[y + 1][x], tile[y - 1][x], tile[y][x + 1], tile[y][x - 1], q[4],
+                               q[0], tile[y + 2][x], tile[y - 2][x], tile[y][x + 2], tile[y][x - 2], P.inv12h2);
+        } else {
+          lphi = apply_regular<T>(phi_in, i, j, k, P);
+        }
+        res = fma(T(P.winv[ci][cj][ck]), s[idx] - lphi, v);
+      }
+      phi_out[idx] = res;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) q[t] = q[t + 1];
+    q[4] = (inb && i + 3 < n) ? phi_in[(long long)(i + 3) * nn + col] : T(0);
   }
 }
+constexpr int kJBX = 32, kJBY = 8, kJIC = 32;
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
@@ -1014,7 +1067,8 @@ void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
   const int block = 256;
   ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
   (void)block;
-  k_jacobi<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(in, s, out, L.typ, L.P);
+  const dim3 grid((L.n + kJBX - 1) / kJBX, (L.n + kJBY - 1) / kJBY, (L.n + kJIC - 1) / kJIC);
+  k_jacobi_tiled<T, kJBX, kJBY, kJIC><<<grid, dim3(kJBX, kJBY), 0, S->stream>>>(in, s, out, L.typ, L.P);
 }
 
 void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {
@@ -1409,7 +1463,7 @@ void cc_default_params(cc_params* p) {
   p->krylov = 0;
   p->krylov_restart = 30;
   p->precision = 0;
-  p->lu_persistent = 1;
+  p->lu_persistent = 0;
 }
 
 const char* cc_status_str(cc_status st) {

@@ -244,7 +244,7 @@ def test_lu_schedules_agree(pair):
     from paper_2410_05865_gb300 import ccmg
     S, H, _, _, prob = pair
     lv = H.levels[0]
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, lu_persistent=0)
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, lu_persistent=1)
     phi = rand_unknowns(lv, 11)
     s = rand_unknowns(lv, 12) * 1e3
     a = dev(to_grid(lv, phi))

@@ -174,6 +174,30 @@ cc_status cc_residual(cc_solver* s, int level, const double* phi, const double* 
 cc_status cc_jacobi(cc_solver* s, int level, const double* phi_in, const double* rhs, double* phi_out);
 /* SMO-2 in place: phi2 <- L22^{-1} (rhs2 - L21 phi1). */
 cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* rhs);
+/* The same SMO-2 step, for callers that must not allocate device memory at the
+ * point of the call: code whose device memory is owned by another allocator or
+ * budget (a framework's caching pool that has reserved the GPU, a fixed-memory
+ * service), or code that cannot afford the implicit synchronisation of
+ * cudaMalloc/cudaFree.  The paper has no counterpart; it is a library service.
+ * The call allocates nothing and uses none of the solver's own LU work vectors:
+ * its four work vectors live in one static device array of the library
+ * (8 MiB, held on every GPU that loads the library until the process exits).
+ *   phi, rhs   device grid arrays of `level` (FP64), as for cc_lu_correction;
+ *              phi is updated in place on the solver's stream.
+ * Limits and behaviour:
+ *   - the level's LU-correction may have at most 262144 phi2 rows; a larger one
+ *     is rejected with CC_ERR_INVALID_ARG and a message (cc_last_error), and
+ *     cc_lu_correction must be used instead; the bottom level is rejected too;
+ *   - the first call on each device looks up the array's device address (the
+ *     solver's device is made current for the call and restored afterwards);
+ *     make that first call before any stream capture;
+ *   - every call, from every solver on that device, shares the one array, so
+ *     calls that overlap on the GPU (other streams, other host threads) race
+ *     and give wrong results; serialise them.  Nothing in the array has to
+ *     start at zero: each call writes what it reads.
+ *   - always uses one launch per tree height (the lu_persistent option is not
+ *     consulted); results agree with cc_lu_correction to rounding. */
+cc_status cc_lu_correction_static(cc_solver* s, int level, double* phi, const double* rhs);
 /* Restrict: coarse[I] = 2^-3 sum of (rhs - L phi) over the phi1 children of I. */
 cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* coarse);
 /* Prolong: phi1 cells of `level` += coarse value of the parent, where the

@@ -83,6 +83,7 @@ SIGNATURES = {
     "cc_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "cc_jacobi": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_lu_correction": (C.c_int, [_P, C.c_int, _P, _P]),
+    "cc_lu_correction_static": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_restrict_residual": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_prolong_add": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_bottom_solve": (C.c_int, [_P, _P, _P]),
@@ -269,6 +270,12 @@ class Solver:
 
     def lu_correction(self, level, phi, s):
         self._check(lib().cc_lu_correction(self._h, level, _ptr(phi), _ptr(s)), "cc_lu_correction")
+
+    def lu_correction_static(self, level, phi, s):
+        """SMO-2 through cc_lu_correction_static: allocates nothing, works in the
+        library's static device array (at most 262144 phi2 rows per level)."""
+        self._check(lib().cc_lu_correction_static(self._h, level, _ptr(phi), _ptr(s)),
+                    "cc_lu_correction_static")
 
     def restrict_residual(self, level, phi, s, coarse):
         self._check(lib().cc_restrict_residual(self._h, level, _ptr(phi), _ptr(s), _ptr(coarse)),

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1442,6 +1443,75 @@ cc_status run_solve(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
   return S->prm.krylov ? gmres_loop(S, phi_out, where, stats) : solve_loop(S, phi_out, where, stats);
 }
 
+// ---------------------------------------- allocation-free LU-correction
+// cc_lu_correction_static keeps its four LU work vectors (b, y, t, x of the
+// triangular solves) in this file-scope device array instead of the vectors
+// cc_setup allocates.  It is part of the module image: every GPU that loads the
+// library holds these 8 MiB until the process exits.
+constexpr int kStaticLuRows = 1 << 18;
+static __device__ __align__(256) double g_lu_scratch[4 * (size_t)kStaticLuRows];
+
+// Device address of g_lu_scratch, looked up once per device.  In host code the
+// name g_lu_scratch is only a host-side stand-in and must never reach a kernel.
+std::mutex g_scratch_mu;
+double* g_scratch_addr[64] = {};
+
+cc_status static_scratch(cc_solver* S, double** out) {
+  if (S->device < 0 || S->device >= 64) return fail(S, CC_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[S->device]) {
+    void* addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_lu_scratch);
+    if (e != cudaSuccess || !addr)
+      return fail(S, CC_ERR_CUDA, std::string("cudaGetSymbolAddress of the static LU scratch: ") +
+                                      cudaGetErrorString(e));
+    g_scratch_addr[S->device] = static_cast<double*>(addr);
+  }
+  *out = g_scratch_addr[S->device];
+  return CC_OK;
+}
+
+// SMO-2 with the per-height schedule, on caller-chosen work vectors.  k_lu_rhs
+// writes all np entries of b before anything reads it, and every later phase
+// writes y, t and x before reading them, so no work vector has to start at zero.
+void lu_solve_into(cc_solver* S, const DevLU& D, const double* s, double* phi, double* b, double* y, double* t,
+                   double* x) {
+  if (D.np == 0) return;
+  const int block = 256;
+  k_lu_rhs<double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, D.np, D.cell, D.rptr, D.rcol, D.rval, s,
+                                                                        phi);
+  const int nsub = std::min(D.nranges, S->nsm * 8);
+  if (D.nranges > 0)
+    k_lu_subtree_fwd<<<nsub, 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals, D.structs, D.pivrow, b, y);
+  auto tasks = [&](int ph, int h) -> std::pair<const Task*, int> {
+    const long long a = D.toff[ph][h], e = D.toff[ph][h + 1];
+    return {D.tasks + a, (int)(e - a)};
+  };
+  for (int h = D.hcut + 1; h <= D.height; ++h) {
+    auto f1 = tasks(T_F1, h);
+    if (f1.second > 0)
+      k_tasks<T_F1><<<grid_for(S, (long long)f1.second * 32, block), block, 0, S->stream>>>(
+          f1.first, f1.second, D.vals, b, D.pivrow, nullptr, y);
+    auto f2 = tasks(T_F2, h);
+    if (f2.second > 0)
+      k_tasks<T_F2><<<grid_for(S, (long long)f2.second * 32, block), block, 0, S->stream>>>(
+          f2.first, f2.second, D.vals, y, nullptr, nullptr, b);
+  }
+  for (int h = D.height; h > D.hcut; --h) {
+    auto b1 = tasks(T_B1, h);
+    if (b1.second > 0)
+      k_tasks<T_B1><<<grid_for(S, (long long)b1.second * 32, block), block, 0, S->stream>>>(
+          b1.first, b1.second, D.vals, x, D.structs, y, t);
+    auto b2 = tasks(T_B2, h);
+    if (b2.second > 0)
+      k_tasks<T_B2><<<grid_for(S, (long long)b2.second * 32, block), block, 0, S->stream>>>(
+          b2.first, b2.second, D.vals, t, nullptr, nullptr, x);
+  }
+  if (D.nranges > 0)
+    k_lu_subtree_bwd<<<nsub, 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals, D.structs, y, x);
+  k_scatter<double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
+}
+
 }  // namespace
 
 thread_local std::string g_setup_err;  // message of the last failed cc_setup on this thread
@@ -2006,6 +2076,33 @@ const char* cc_profile_entry(const cc_solver* S, int k, long long* launches, dou
   if (ms) *ms = S->prof_ms[k];
   if (bytes) *bytes = S->prof_bytes[k];
   return kProfNames[k];
+}
+
+cc_status cc_lu_correction_static(cc_solver* S, int level, double* phi, const double* rhs) {
+  if (!S || !phi || !rhs) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
+  const DevLU& D = S->lev[level].lu;
+  if (D.np > kStaticLuRows)
+    return fail(S, CC_ERR_INVALID_ARG,
+                "cc_lu_correction_static: level " + std::to_string(level) + " has " + std::to_string(D.np) +
+                    " phi2 rows, more than the " + std::to_string(kStaticLuRows) +
+                    " its static work array holds; use cc_lu_correction");
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
+  if (prev != S->device) CK(cudaSetDevice(S->device));
+  double* w = nullptr;
+  st = static_scratch(S, &w);
+  if (st == CC_OK) {
+    const size_t R = (size_t)kStaticLuRows;
+    lu_solve_into(S, D, rhs, phi, w, w + R, w + 2 * R, w + 3 * R);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(S, CC_ERR_CUDA, std::string("cc_lu_correction_static: ") + cudaGetErrorString(e));
+  }
+  if (prev != S->device) cudaSetDevice(prev);
+  return st;
 }
 
 }  // extern "C"

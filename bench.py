@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-n", type=int, default=64, help="grid of the oracle's CPU sample")
-    ap.add_argument("--precision", type=int, default=1, help="0 FP64 V-cycle, 1 FP32 grid work + FP64 LU/outer")
+    ap.add_argument("--precision", type=int, default=2,
+                    help="0 FP64 V-cycle; 1 FP32 grid work, FP64 LU-corrections; 2 FP32 grid work and "
+                         "LU-correction factors (FP64 PLG rows, bottom solve and outer residual)")
     ap.add_argument("--krylov", type=int, default=1, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
     ap.add_argument("--min-n", type=int, default=32, help="coarsening stops before n < min-n")
     ap.add_argument("--restart", type=int, default=30)
@@ -352,13 +354,16 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic",
             "config": {"workload": workload(args, n),
                        "n": n, "unknowns": N, "levels": [info.n[m] for m in range(info.n_levels)],
                        "phi2_per_level": [info.n_phi2[m] for m in range(info.n_levels)],
                        "lu_entries_per_level": [info.lu_entries[m] for m in range(info.n_levels)],
                        "v_cycles": iters[-1], "omega": 0.5, "nu1": 3, "nu2": 3,
-                       "precision": ["fp64", "fp32 grid work, fp64 LU-corrections/outer residual"][args.precision],
+                       "precision": ["fp64",
+                                     "fp32 grid work; fp64 LU-corrections, bottom solve, outer residual",
+                                     "fp32 grid work and LU-correction factors; fp64 PLG rows, bottom solve, "
+                                     "outer residual"][args.precision],
                        "outer": ["Alg. Multigrid", f"GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
                        "plain_fp64_same_solver": fp64,
                        "setup_s": round(setup_s, 1), "parallelism": f"replicas x{world}",

@@ -48,7 +48,7 @@ typedef enum {
   CC_ERR_NOT_CONVERGED = 6,
   CC_ERR_DIVERGED = 7,     /* non-finite residual */
   CC_ERR_MERGE = 8,        /* cell merging could not make every cell theta-proper */
-  CC_ERR_TIMEOUT = 9
+  CC_ERR_TIMEOUT = 9       /* reserved: no call returns it at present */
 } cc_status;
 
 enum { CC_DIRICHLET = 0, CC_NEUMANN = 1 };
@@ -82,9 +82,10 @@ typedef struct {
   int krylov_restart;/* GMRES restart length m (30) */
   int precision;     /* 0: FP64 V-cycle; 1: FP32 grid work inside the V-cycle (Jacobi,
                         restriction, prolongation) with FP64 LU-corrections, bottom
-                        solve and outer residual (defect correction) (0) */
-  int lu_persistent; /* 1: each triangular solve is one launch with dynamic task fetch
-                        and bounded waits; 0: one launch per tree height and phase (0) */
+                        solve and outer residual (defect correction); 2: as 1, and
+                        the LU-corrections of the finer levels store and apply their
+                        factors in FP32 (their right-hand sides, built from the PLG
+                        rows, the bottom solve and the outer residual stay FP64) (0) */
 } cc_params;
 
 typedef struct {
@@ -180,8 +181,8 @@ cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* r
  * service), or code that cannot afford the implicit synchronisation of
  * cudaMalloc/cudaFree.  The paper has no counterpart; it is a library service.
  * The call allocates nothing and uses none of the solver's own LU work vectors:
- * its four work vectors live in one static device array of the library
- * (8 MiB, held on every GPU that loads the library until the process exits).
+ * its two work vectors live in one static device array of the library
+ * (4 MiB, held on every GPU that loads the library until the process exits).
  *   phi, rhs   device grid arrays of `level` (FP64), as for cc_lu_correction;
  *              phi is updated in place on the solver's stream.
  * Limits and behaviour:
@@ -195,8 +196,8 @@ cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* r
  *     calls that overlap on the GPU (other streams, other host threads) race
  *     and give wrong results; serialise them.  Nothing in the array has to
  *     start at zero: each call writes what it reads.
- *   - always uses one launch per tree height (the lu_persistent option is not
- *     consulted); results agree with cc_lu_correction to rounding. */
+ *   - results agree with cc_lu_correction to rounding (both add partial dot
+ *     products with atomics, in an order that varies from call to call). */
 cc_status cc_lu_correction_static(cc_solver* s, int level, double* phi, const double* rhs);
 /* Restrict: coarse[I] = 2^-3 sum of (rhs - L phi) over the phi1 children of I. */
 cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* coarse);

@@ -29,13 +29,53 @@ using namespace ccmg;
 namespace {
 
 // ------------------------------------------------------------------ kernels
+// The FP32 kernels read the float copies of the tables: on this GPU an FP64
+// instruction (even a compare or a conversion) issues at a small fraction of the
+// FP32 rate, so the FP32 sweeps must not touch FP64 at all.
 struct StencilP {
   int n;
   double inv12h2;
+  float inv12h2_f;
+  signed char lo[3][5], hi[3][5];  // window of nonzero offsets per axis and position class
   double c[3][5][7];  // per axis, position class, offsets -3..3 (times 12 h^2)
+  float cf[3][5][7];
   double g[3][5];     // coefficient of the nearer wall's <g> (times 12 h^2)
   double winv[5][5][5];  // omega / D for each combination of position classes
+  float winvf[5][5][5];
 };
+
+template <class T>
+__device__ __forceinline__ T st_coef(const StencilP& P, int d, int c, int o);
+template <>
+__device__ __forceinline__ double st_coef<double>(const StencilP& P, int d, int c, int o) {
+  return P.c[d][c][o];
+}
+template <>
+__device__ __forceinline__ float st_coef<float>(const StencilP& P, int d, int c, int o) {
+  return P.cf[d][c][o];
+}
+template <class T>
+__device__ __forceinline__ T st_inv(const StencilP& P);
+template <>
+__device__ __forceinline__ double st_inv<double>(const StencilP& P) {
+  return P.inv12h2;
+}
+template <>
+__device__ __forceinline__ float st_inv<float>(const StencilP& P) {
+  return P.inv12h2_f;
+}
+template <class T>
+__device__ __forceinline__ T st_winv(const StencilP& P, int a, int b, int c);
+template <>
+__device__ __forceinline__ double st_winv<double>(const StencilP& P, int a, int b, int c) {
+  return P.winv[a][b][c];
+}
+template <>
+__device__ __forceinline__ float st_winv<float>(const StencilP& P, int a, int b, int c) {
+  return P.winvf[a][b][c];
+}
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 __device__ __forceinline__ int pos_class(int p, int n) {
   return p == 0 ? 0 : (p == 1 ? 1 : (p == n - 2 ? 3 : (p == n - 1 ? 4 : 2)));
@@ -45,10 +85,10 @@ __device__ __forceinline__ int pos_class(int p, int n) {
 // the neighbour sums taken in the order +i, -i, +j, -j, +k, -k so that every kernel rounds alike.
 template <class T>
 __device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1, T km1, T ip2, T im2, T jp2, T jm2,
-                                        T kp2, T km2, double inv12h2) {
+                                        T kp2, T km2, T inv12h2) {
   const T s1 = ip1 + im1 + jp1 + jm1 + kp1 + km1;
   const T s2 = ip2 + im2 + jp2 + jm2 + kp2 + km2;
-  return (T(16) * s1 - s2 - T(90) * c0) * T(inv12h2);
+  return (T(16) * s1 - s2 - T(90) * c0) * inv12h2;
 }
 
 // (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
@@ -61,34 +101,34 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
   if (ci == 2 && cj == 2 && ck == 2) {
     return interior13<T>(phi[idx], phi[idx + nn], phi[idx - nn], phi[idx + n], phi[idx - n], phi[idx + 1],
                          phi[idx - 1], phi[idx + 2 * nn], phi[idx - 2 * nn], phi[idx + 2 * n], phi[idx - 2 * n],
-                         phi[idx + 2], phi[idx - 2], P.inv12h2);
+                         phi[idx + 2], phi[idx - 2], st_inv<T>(P));
   }
+  // near the box: the ghost-eliminated 1-D rows, over each row's window of nonzero offsets
   const int cls[3] = {ci, cj, ck};
   const long long stride[3] = {nn, (long long)n, 1};
   T acc = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double* c = P.c[d][cls[d]];
-#pragma unroll
-    for (int o = -3; o <= 3; ++o) {
-      const double w = c[o + 3];
-      if (w != 0.0) acc += T(w) * phi[idx + o * stride[d]];
-    }
+    const int c = cls[d];
+    for (int o = P.lo[d][c]; o <= P.hi[d][c]; ++o) acc += st_coef<T>(P, d, c, o + 3) * phi[idx + o * stride[d]];
   }
-  return acc * T(P.inv12h2);
+  return acc * st_inv<T>(P);
 }
 
 // Grid kernels run on a 3-D launch: threads along k, blockIdx.y = j, blockIdx.z = i.
 // SMO-1 with 2.5-D blocking: a BY x BX tile of (j, k) columns marches along i over
 // IC planes.  Plane i (with a 2-cell halo in j and k) is staged in shared memory,
 // the i -+ 1, 2 neighbours of each column ride in a register queue, so each value
-// is read from HBM/L2 about once instead of through 13 scattered loads.  Cells
+// is read from HBM/L2 about once instead of through 13 scattered loads.  The
+// loads of plane i+1 (tile part, s and typ) are issued before plane i is
+// computed, so one memory latency per plane overlaps the arithmetic.  Cells
 // whose row is not the interior row (near the box) take apply_regular.
 template <class T, int BX, int BY, int IC>
 __global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ phi_in, const T* __restrict__ s,
                                                            T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
                                                            StencilP P) {
-  __shared__ T tile[BY + 4][BX + 4];
+  constexpr int TW = BX + 4, NT = (BY + 4) * TW, PER = (NT + BX * BY - 1) / (BX * BY);
+  __shared__ T tile[BY + 4][TW];
   const int n = P.n;
   const long long nn = (long long)n * n;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -98,6 +138,24 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ 
   const int i1 = min(i0 + IC, n);
   const bool inb = k < n && j < n;
   const long long col = (long long)j * n + k;
+  // this thread's tile slots e = tid + p BX BY: in-plane offset, or -1 outside the grid / tile
+  long long goff[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = tid + p * BX * BY;
+    const int ly = e / TW, lx = e - ly * TW;
+    const int jj = j0 + ly - 2, kk = k0 + lx - 2;
+    goff[p] = (e < NT && jj >= 0 && jj < n && kk >= 0 && kk < n) ? (long long)jj * n + kk : -1;
+  }
+  T pre[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) pre[p] = goff[p] >= 0 ? phi_in[(long long)i0 * nn + goff[p]] : T(0);
+  T s_nx = T(0);
+  uint8_t t_nx = 0;
+  if (inb) {
+    s_nx = s[(long long)i0 * nn + col];
+    t_nx = typ[(long long)i0 * nn + col];
+  }
   // q[t] = phi(i - 2 + t) of this column; q[2] is also in the tile
   T q[5];
 #pragma unroll
@@ -108,28 +166,37 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ 
   const int cj = pos_class(j, n), ck = pos_class(k, n);
   for (int i = i0; i < i1; ++i) {
     __syncthreads();
-    for (int e = tid; e < (BY + 4) * (BX + 4); e += BX * BY) {
-      const int ly = e / (BX + 4), lx = e - ly * (BX + 4);
-      const int jj = j0 + ly - 2, kk = k0 + lx - 2;
-      tile[ly][lx] = (jj >= 0 && jj < n && kk >= 0 && kk < n) ? phi_in[(long long)i * nn + (long long)jj * n + kk]
-                                                              : T(0);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = tid + p * BX * BY;
+      if (e < NT) (&tile[0][0])[e] = pre[p];
     }
     __syncthreads();
+    const T s_cur = s_nx;
+    const uint8_t t_cur = t_nx;
+    if (i + 1 < i1) {
+#pragma unroll
+      for (int p = 0; p < PER; ++p) pre[p] = goff[p] >= 0 ? phi_in[(long long)(i + 1) * nn + goff[p]] : T(0);
+      if (inb) {
+        s_nx = s[(long long)(i + 1) * nn + col];
+        t_nx = typ[(long long)(i + 1) * nn + col];
+      }
+    }
     if (inb) {
       const long long idx = (long long)i * nn + col;
       const T v = q[2];
       T res = v;
-      if (typ[idx] == 1) {
+      if (t_cur == 1) {
         const int ci = pos_class(i, n);
         T lphi;
         if (ci == 2 && cj == 2 && ck == 2) {
           const int y = ty + 2, x = tx + 2;
           lphi = interior13<T>(v, q[3], q[1], tile[y + 1][x], tile[y - 1][x], tile[y][x + 1], tile[y][x - 1], q[4],
-                               q[0], tile[y + 2][x], tile[y - 2][x], tile[y][x + 2], tile[y][x - 2], P.inv12h2);
+                               q[0], tile[y + 2][x], tile[y - 2][x], tile[y][x + 2], tile[y][x - 2], st_inv<T>(P));
         } else {
           lphi = apply_regular<T>(phi_in, i, j, k, P);
         }
-        res = fma(T(P.winv[ci][cj][ck]), s[idx] - lphi, v);
+        res = fma_t(st_winv<T>(P, ci, cj, ck), s_cur - lphi, v);
       }
       phi_out[idx] = res;
     }
@@ -138,7 +205,7 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ 
     q[4] = (inb && i + 3 < n) ? phi_in[(long long)(i + 3) * nn + col] : T(0);
   }
 }
-constexpr int kJBX = 32, kJBY = 8, kJIC = 32;
+constexpr int kJBX = 32, kJBY = 8, kJIC = 16;
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
@@ -206,20 +273,22 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
 }
 
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
-// (FP64 accumulation whatever the grid type: the LU-correction stays FP64)
-template <class T>
-__global__ void k_lu_rhs(double* __restrict__ b, int np, const int* __restrict__ cell, const int* __restrict__ ptr,
-                         const int* __restrict__ col, const double* __restrict__ val, const T* __restrict__ s,
-                         const T* __restrict__ phi) {
+// The PLG rows are applied in FP64 whatever the grid type; b is stored in the
+// LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
+template <class T, class TW>
+__global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
+                         const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
+                         const T* __restrict__ s, const T* __restrict__ phi) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     double v = (double)s[cell[p]];
     for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
-    b[p] = v;
+    b[p] = (TW)v;
+    x[p] = TW(0);
   }
 }
 
-template <class T>
-__global__ void k_scatter(const double* __restrict__ x, int np, const int* __restrict__ cell, T* __restrict__ phi) {
+template <class T, class TW>
+__global__ void k_scatter(const TW* __restrict__ x, int np, const int* __restrict__ cell, T* __restrict__ phi) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) phi[cell[p]] = (T)x[p];
 }
 
@@ -233,223 +302,63 @@ __global__ void k_axpy_f(double* __restrict__ phi, const float* __restrict__ e, 
     phi[i] += (double)e[i];
 }
 
+// ---- supernodal triangular solves in block-elimination form (SMO-2, bottom solve)
+// Per supernode s (first ND position f0, k rows, m struct rows): the forward
+// sweep (children first) is b_struct -= W b_s, the backward sweep (parents
+// first) is x_s = G b_s - V x_struct (the pivoting P_s is folded into the
+// columns of G and W).  Blocks are stored column-major.  Every sweep is one
+// launch per tree height over warp tasks; a task is a tile of up to 32 rows x
+// kSegCols columns of one block.  Lane r owns row r of the tile and runs down
+// its columns: each column is one coalesced load, the source entry is shared
+// by a warp shuffle, and no cross-lane reduction is needed (on this GPU the FP64
+// adds of a shuffle reduction would cost as much as the products).  Partial row
+// sums go to the outputs with atomic adds.
+constexpr int kSegCols = 64;
+
 struct Task {
-  long long moff;  // first value of the matrix row
-  int ncols;
-  int xoff;        // first input position (or first gather index)
-  int out;         // output position
-  int pad;
+  long long moff;  // entry (r0, c0) of the column-major block
+  int ld;          // rows of the block (column stride)
+  int nrows;       // rows in the tile (<= 32)
+  int ncols;       // columns in the tile (<= kSegCols)
+  int soff;        // source: first b position (G, W tiles) or first structs index (V tiles)
+  int out;         // outputs: first x position (G, V tiles) or first structs index (W tiles)
+  int src;         // 0: + G b_s, 1: - V x_struct (gathered), 2: - W b_s (forward, scattered into b)
 };
 
-enum { T_F1 = 0, T_F2 = 1, T_B1 = 2, T_B2 = 3 };
-
-// One warp per matrix row: dot product of a dense row with a vector segment.
-template <int MODE>
-__global__ void k_tasks(const Task* __restrict__ tasks, int ntasks, const double* __restrict__ vals,
-                        const double* __restrict__ xin, const int* __restrict__ gidx, const double* __restrict__ yin,
-                        double* __restrict__ out) {
+template <bool FWD, class TV>
+__global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3) k_tasks(const Task* __restrict__ tasks, int ntasks, const TV* __restrict__ vals,
+                                               const int* __restrict__ structs, TV* b, TV* x) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = warp; t < ntasks; t += nwarps) {
     const Task tk = tasks[t];
-    const double* __restrict__ row = vals + tk.moff;
-    double acc = 0.0;
-    if (MODE == T_B1 || MODE == T_F1) {
-      const int* __restrict__ g = gidx + tk.xoff;
-      for (int j = lane; j < tk.ncols; j += 32) acc += row[j] * xin[g[j]];
-    } else {
-      const double* __restrict__ x = xin + tk.xoff;
-      for (int j = lane; j < tk.ncols; j += 32) acc += row[j] * x[j];
-    }
+    const int nc = tk.ncols, ld = tk.ld;
+    const bool gather = !FWD && tk.src == 1;
+    const bool mine = lane < tk.nrows;
+    const TV* __restrict__ col = vals + tk.moff + (mine ? lane : 0);
+    TV acc = TV(0);
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      // lane l holds source entry c0 + l
+      const int c = c0 + lane;
+      TV sv = TV(0);
+      if (c < nc) sv = gather ? x[structs[tk.soff + c]] : b[tk.soff + c];
+      const int cn = min(32, nc - c0);
+      // all loads of a batch are issued before the first product uses one
+      constexpr int kBatch = sizeof(TV) == 4 ? 32 : 8;
+      for (int i = 0; i < cn; i += kBatch) {
+        TV mv[kBatch];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      if (MODE == T_F1 || MODE == T_B2)
-        out[tk.out] = acc;
-      else if (MODE == T_F2)
-        atomicAdd(out + tk.out, -acc);
-      else
-        out[tk.out] = yin[tk.out] - acc;
-    }
-  }
-}
-
-// ---- fused supernode solves: one CTA runs both phases of a small supernode
-// (diagonal-block product into shared memory, then the off-diagonal block).
-constexpr int kSmallK = 256;  // supernodes with at most this many columns are "small"
-
-struct SnMeta {
-  long long linv, uinv, l21, u12, st;  // value offsets and struct offset
-  int first, k, m, pad;
-};
-
-__device__ __forceinline__ double warp_sum(double a) {
+        for (int u = 0; u < kBatch; ++u) mv[u] = i + u < cn ? __ldcs(col + (long long)(c0 + i + u) * ld) : TV(0);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
-__device__ void fwd_one(const SnMeta& sm, const double* __restrict__ vals, const int* __restrict__ structs,
-                        const int* __restrict__ pivrow, double* b, double* __restrict__ y, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int k = sm.k, f0 = sm.first;
-  for (int t = warp; t < k; t += nw) {
-    const double* row = vals + sm.linv + (long long)t * k;
-    double a = 0.0;
-    for (int c = lane; c <= t; c += 32) a += row[c] * b[pivrow[f0 + c]];
-    a = warp_sum(a);
-    if (lane == 0) {
-      y[f0 + t] = a;
-      sh[t] = a;
-    }
-  }
-  __syncthreads();
-  for (int r = warp; r < sm.m; r += nw) {
-    const double* row = vals + sm.l21 + (long long)r * k;
-    double a = 0.0;
-    for (int c = lane; c < k; c += 32) a += row[c] * sh[c];
-    a = warp_sum(a);
-    if (lane == 0) atomicAdd(b + structs[sm.st + r], -a);
-  }
-  __syncthreads();
-}
-
-__device__ void bwd_one(const SnMeta& sm, const double* __restrict__ vals, const int* __restrict__ structs,
-                        const double* __restrict__ y, double* x, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int k = sm.k, f0 = sm.first, m = sm.m;
-  for (int r = warp; r < k; r += nw) {
-    const double* row = vals + sm.u12 + (long long)r * m;
-    double a = 0.0;
-    for (int c = lane; c < m; c += 32) a += row[c] * x[structs[sm.st + c]];
-    a = warp_sum(a);
-    if (lane == 0) sh[r] = y[f0 + r] - a;
-  }
-  __syncthreads();
-  for (int r = warp; r < k; r += nw) {
-    const double* row = vals + sm.uinv + (long long)r * k;
-    double a = 0.0;
-    for (int c = r + lane; c < k; c += 32) a += row[c] * sh[c];
-    a = warp_sum(a);
-    if (lane == 0) x[f0 + r] = a;
-  }
-  __syncthreads();
-}
-
-// one CTA per subtree (a contiguous postorder range [lo, hi] of small supernodes)
-__global__ void k_lu_subtree_fwd(const SnMeta* __restrict__ meta, const int2* __restrict__ ranges, int nr,
-                                 const double* __restrict__ vals, const int* __restrict__ structs,
-                                 const int* __restrict__ pivrow, double* b, double* __restrict__ y) {
-  __shared__ double sh[kSmallK];
-  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
-    const int2 rg = ranges[r];
-    for (int s = rg.x; s <= rg.y; ++s) fwd_one(meta[s], vals, structs, pivrow, b, y, sh);
-  }
-}
-
-__global__ void k_lu_subtree_bwd(const SnMeta* __restrict__ meta, const int2* __restrict__ ranges, int nr,
-                                 const double* __restrict__ vals, const int* __restrict__ structs,
-                                 const double* __restrict__ y, double* x) {
-  __shared__ double sh[kSmallK];
-  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
-    const int2 rg = ranges[r];
-    for (int s = rg.y; s >= rg.x; --s) bwd_one(meta[s], vals, structs, y, x, sh);
-  }
-}
-
-
-// ---- one-launch supernodal triangular solve (forward then backward) with
-// dynamic task fetch.  Tasks are stored in dependency order: for each height
-// (ascending) the forward diagonal rows (F1) then the off-diagonal rows (F2);
-// then for each height (descending) the backward off-diagonal rows (B1) then
-// the diagonal rows (B2).  A warp takes the next task from a global counter,
-// so every task it may wait on was taken earlier by a running warp: the waits
-// always end.  Waits are bounded anyway: on exhaustion the kernel raises
-// err[0] and returns (the host reports CC_ERR_TIMEOUT).
-struct PTask {
-  long long moff;
-  int ncols;
-  int xoff;
-  int out;
-  int kind;  // 0 F1, 1 F2, 2 B1, 3 B2
-  int sn;    // supernode
-  int gate;  // F1/B1: index into the gate thresholds; F2/B2: number of rows of the supernode
-  int k;     // rows of the supernode (B1 also waits for the supernode's whole forward step)
-};
-
-__device__ __forceinline__ bool wait_geq(const unsigned int* p, unsigned int v, unsigned int* err) {
-  long long spins = 0;
-  while (*(volatile const unsigned int*)p < v) {
-    if (*(volatile unsigned int*)err) return false;
-    if (++spins > (1ll << 24)) {
-      atomicExch(err, 1u);
-      return false;
-    }
-    __nanosleep(64);
-  }
-  __threadfence();
-  return true;
-}
-
-__global__ void __launch_bounds__(256) k_lu_persistent(const PTask* __restrict__ tasks, int ntasks,
-                                                       const double* __restrict__ vals, const int* __restrict__ structs,
-                                                       const int* __restrict__ pivrow, double* b, double* y, double* t,
-                                                       double* x, unsigned int* ctr /* [0] next task, [1] F2 done,
-                                                       [2] B2 done, then per supernode: F1 rows done, B1 rows done */,
-                                                       const unsigned int* __restrict__ gates, int nsuper,
-                                                       unsigned int* err) {
-  const int lane = threadIdx.x & 31;
-  unsigned int* f1done = ctr + 4;
-  unsigned int* b1done = ctr + 4 + nsuper;
-  while (true) {
-    int ti = 0;
-    if (lane == 0) ti = (int)atomicAdd(ctr, 1u);
-    ti = __shfl_sync(0xffffffffu, ti, 0);
-    if (ti >= ntasks) return;
-    const PTask tk = tasks[ti];
-    bool ok = true;
-    if (lane == 0) {
-      if (tk.kind == 0) ok = wait_geq(ctr + 1, gates[tk.gate], err);        // all F2 of lower heights
-      else if (tk.kind == 1) ok = wait_geq(f1done + tk.sn, tk.gate, err);  // y_s complete
-      else if (tk.kind == 2)  // all B2 of higher heights, and y_s complete
-        ok = wait_geq(ctr + 2, gates[tk.gate], err) && wait_geq(f1done + tk.sn, tk.k, err);
-      else ok = wait_geq(b1done + tk.sn, tk.gate, err);                    // t_s complete
-    }
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    if (!ok) return;
-    __threadfence();
-    const double* __restrict__ row = vals + tk.moff;
-    double a = 0.0;
-    if (tk.kind == 0) {
-      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(b + pivrow[tk.xoff + c]);
-    } else if (tk.kind == 1) {
-      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(y + tk.xoff + c);
-    } else if (tk.kind == 2) {
-      const int* __restrict__ g = structs + tk.xoff;
-      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(x + g[c]);
-    } else {
-      for (int c = lane; c < tk.ncols; c += 32) a += row[c] * __ldcg(t + tk.xoff + c);
-    }
-    a = warp_sum(a);
-    if (lane == 0) {
-      if (tk.kind == 0) {
-        y[tk.out] = a;
-        __threadfence();
-        atomicAdd(f1done + tk.sn, 1u);
-      } else if (tk.kind == 1) {
-        atomicAdd(b + tk.out, -a);
-        __threadfence();
-        atomicAdd(ctr + 1, 1u);
-      } else if (tk.kind == 2) {
-        t[tk.out] = __ldcg(y + tk.out) - a;
-        __threadfence();
-        atomicAdd(b1done + tk.sn, 1u);
-      } else {
-        x[tk.out] = a;
-        __threadfence();
-        atomicAdd(ctr + 2, 1u);
+        for (int u = 0; u < kBatch; ++u) acc = fma_t(mv[u], __shfl_sync(0xffffffffu, sv, (i + u) & 31), acc);
       }
+    }
+    if (mine) {
+      if (FWD)
+        atomicAdd(b + structs[tk.out + lane], -acc);
+      else
+        atomicAdd(x + tk.out + lane, tk.src == 1 ? -acc : acc);
     }
   }
 }
@@ -569,33 +478,20 @@ struct DBuf {
 struct DevLU {
   int np = 0;       // dimension
   int height = -1;
+  bool f32 = false;          // factors and work vectors in FP32 (vals32, b32, x32)
   double* vals = nullptr;
+  float* vals32 = nullptr;
   int* structs = nullptr;
-  int* pivrow = nullptr;
   Task* tasks = nullptr;
-  std::vector<long long> toff[4];  // per phase: offsets by height (height+2)
-  std::vector<double> tbytes[4];   // per phase and height: algorithmic bytes of one launch
-  long long ntasks[4] = {0, 0, 0, 0};
-  double *b = nullptr, *y = nullptr, *t = nullptr, *x = nullptr;
+  std::vector<long long> toff[2];  // per sweep (0 forward, 1 backward): task offsets by height (height+2)
+  std::vector<double> tbytes[2];   // per sweep and height: algorithmic bytes of one launch
+  double *b = nullptr, *x = nullptr;  // work vectors of the sweeps
+  float *b32 = nullptr, *x32 = nullptr;
   int* cell = nullptr;  // ND position -> grid index
   int *rptr = nullptr, *rcol = nullptr;
   double* rval = nullptr;
   long long entries = 0;
   long long rnnz = 0;
-  // fused small-supernode schedule
-  SnMeta* meta = nullptr;
-  int2* ranges = nullptr;
-  int nranges = 0;
-  int hcut = -1;                      // heights <= hcut run in the subtree kernels
-  double bytes_subtree = 0;           // algorithmic bytes of one subtree launch (fwd or bwd)
-  // one-launch schedule
-  PTask* ptasks = nullptr;
-  int nptasks = 0;
-  unsigned int* pgates = nullptr;
-  unsigned int* pctr = nullptr;       // 4 + 2 nsuper counters
-  int nsuper = 0;
-  double pbytes = 0;
-  long long task_bytes[4] = {0, 0, 0, 0};  // algorithmic bytes per solve phase (matrix + vectors)
 };
 
 struct DevLevel {
@@ -628,22 +524,17 @@ enum Prof {
   P_RESTRICT,
   P_PROLONG,
   P_LURHS,
-  P_F1,
-  P_F2,
-  P_B1,
-  P_B2,
+  P_FWD,
+  P_BWD,
   P_SCATTER,
   P_AXPY,
   P_NORM,
   P_RHS,
-  P_SUBTREE,
-  P_PERSIST,
   P_COUNT
 };
-const char* kProfNames[P_COUNT] = {"jacobi",      "resid_phi1", "resid_phi2", "restrict", "prolong",
-                                   "lu_rhs",      "trsv_fwd_diag", "trsv_fwd_update", "trsv_bwd_update",
-                                   "trsv_bwd_diag", "lu_scatter", "axpy", "norm", "rhs",
-                                   "lu_subtree", "lu_persistent"};
+const char* kProfNames[P_COUNT] = {"jacobi", "resid_phi1", "resid_phi2", "restrict", "prolong",
+                                   "lu_rhs", "lu_fwd",     "lu_bwd",     "lu_scatter", "axpy",
+                                   "norm",   "rhs"};
 
 }  // namespace
 
@@ -660,7 +551,6 @@ struct cc_solver {
   // finest level extras
   double *r = nullptr, *phi = nullptr, *s0 = nullptr, *f = nullptr, *gbox = nullptr, *gpatch = nullptr;
   double* norm = nullptr;   // device scalar
-  unsigned int* err_flag = nullptr;  // raised by a bounded wait that ran out
   double* hnorm = nullptr;  // pinned host scalar
   int ngroups = 0;
   int *g_owner = nullptr, *g_ptr = nullptr, *g_part = nullptr;
@@ -674,12 +564,14 @@ struct cc_solver {
   cc_info info;
   // graphs
   cudaGraphExec_t cycle_exec = nullptr;
+  cudaGraphExec_t prec_exec = nullptr;  // one V-cycle from kin into lev[0].e (GMRES)
   // Krylov workspace (allocated on first use)
   double* kV = nullptr;     // (m+1) grid vectors
   double* kw = nullptr;     // work vector
   double* kdots = nullptr;  // device scalars
   double* khdots = nullptr; // pinned copy
   double* kzero = nullptr;  // a zero grid array
+  double* kin = nullptr;    // fixed input of the captured preconditioner
   int km = 0;
   // profiling
   bool prof = false;
@@ -786,7 +678,22 @@ StencilP make_stencil(const Level& L, double omega) {
       for (int cc = 0; cc < 5; ++cc) {
         const double dg = (P.c[0][a][3] + P.c[1][b][3] + P.c[2][cc][3]) * P.inv12h2;
         P.winv[a][b][cc] = omega / dg;
+        P.winvf[a][b][cc] = (float)P.winv[a][b][cc];
       }
+  P.inv12h2_f = (float)P.inv12h2;
+  for (int d = 0; d < 3; ++d)
+    for (int c = 0; c < 5; ++c) {
+      int lo = 4, hi = -4;
+      for (int o = -3; o <= 3; ++o) {
+        P.cf[d][c][o + 3] = (float)P.c[d][c][o + 3];
+        if (P.c[d][c][o + 3] != 0.0) {
+          lo = std::min(lo, o);
+          hi = std::max(hi, o);
+        }
+      }
+      P.lo[d][c] = (signed char)lo;
+      P.hi[d][c] = (signed char)hi;
+    }
   return P;
 }
 
@@ -835,157 +742,66 @@ void full_operator(const Level& L, const StencilP& P, std::vector<int>& uid, std
 }
 
 cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<int>& pos_cell,
-                    const std::vector<int>& rptr, const std::vector<int>& rcol, const std::vector<double>& rval) {
+                    const std::vector<int>& rptr, const std::vector<int>& rcol, const std::vector<double>& rval,
+                    bool f32) {
   D.np = F.n;
   D.height = F.height;
   D.entries = F.nnz_factor;
+  D.f32 = f32;
   cc_status st;
-  if ((st = dupload(S, &D.vals, F.vals))) return st;
+  if (f32) {
+    std::vector<float> v32(F.vals.begin(), F.vals.end());
+    if ((st = dupload(S, &D.vals32, v32))) return st;
+  } else if ((st = dupload(S, &D.vals, F.vals))) {
+    return st;
+  }
   if ((st = dupload(S, &D.structs, F.structs))) return st;
-  if ((st = dupload(S, &D.pivrow, F.pivrow))) return st;
-  std::vector<Task> all;
-  for (int ph = 0; ph < 4; ++ph) D.toff[ph].assign(F.height + 2, 0);
-  std::vector<Task> per[4];
-  std::vector<std::vector<Task>> byh[4];
-  for (int ph = 0; ph < 4; ++ph) byh[ph].assign(F.height + 1, {});
-  // small supernodes run fused (subtree kernel below hcut, per-height kernels above)
-  std::vector<SnMeta> meta(F.nsuper);
-  std::vector<int> lo(F.nsuper);
-  std::vector<char> small(F.nsuper);
-  std::vector<int> parent(F.nsuper, -1);
-  for (int s = 0; s < F.nsuper; ++s) {
-    const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
-    const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
-    meta[s] = {F.off_linv[s], F.off_uinv[s], F.off_l21[s], F.off_u12[s], F.sn_struct[s], f0, k, m, 0};
-    small[s] = k <= kSmallK;
-    lo[s] = s;
+  if (!F.structs.empty() && F.sn_struct[F.nsuper] > (long long)INT32_MAX) {
+    S->err = "LU structure too large for 32-bit task indices";
+    return CC_ERR_INVALID_ARG;
   }
-  // postorder numbering: the subtree of s is the contiguous range [lo[s], s]
-  for (int s = 0; s < F.nsuper; ++s) {
-    parent[s] = F.sn_parent[s];
-    if (parent[s] >= 0) lo[parent[s]] = std::min(lo[parent[s]], lo[s]);
-  }
-  // hcut: the largest height such that every supernode at or below it is small
-  // and the subtrees rooted there still number at least 8 per SM
-  std::vector<int> allsmall(F.height + 1, 1);
-  for (int s = 0; s < F.nsuper; ++s)
-    if (!small[s]) allsmall[F.sn_height[s]] = 0;
-  D.hcut = -1;
-  for (int h = 0; h <= F.height; ++h) {
-    if (!allsmall[h]) break;
-    int roots = 0;
-    for (int s = 0; s < F.nsuper; ++s)
-      if (F.sn_height[s] <= h && (parent[s] < 0 || F.sn_height[parent[s]] > h)) ++roots;
-    if (h > 0 && roots < 8 * S->nsm) break;
-    D.hcut = h;
-  }
-  auto sn_bytes = [&](int s, bool fwd) {
-    const SnMeta& q = meta[s];
-    double b = fwd ? 8.0 * q.k * (q.k + 1) / 2 + 8.0 * (double)q.m * q.k : 8.0 * q.k * (q.k + 1) / 2 + 8.0 * (double)q.m * q.k;
-    return b + 12.0 * q.k + 12.0 * q.m;
+  // warp tasks of the per-height launches: tiles of at most 32 rows x kSegCols
+  // columns of the column-major blocks
+  std::vector<std::vector<Task>> byh[2];
+  for (int sw = 0; sw < 2; ++sw) byh[sw].assign(F.height + 1, {});
+  auto tiles = [&](std::vector<Task>& out, long long off, int rows, int cols, int soff0, int out0, int src) {
+    for (int r0 = 0; r0 < rows; r0 += 32)
+      for (int c0 = 0; c0 < cols; c0 += kSegCols)
+        out.push_back({off + (long long)c0 * rows + r0, rows, std::min(32, rows - r0),
+                       std::min(kSegCols, cols - c0), soff0 + c0, out0 + r0, src});
   };
-  std::vector<int2> ranges;
-  D.bytes_subtree = 0;
   for (int s = 0; s < F.nsuper; ++s) {
-    if (F.sn_height[s] <= D.hcut) D.bytes_subtree += sn_bytes(s, true);
-    if (F.sn_height[s] <= D.hcut && (parent[s] < 0 || F.sn_height[parent[s]] > D.hcut)) ranges.push_back(make_int2(lo[s], s));
-  }
-  D.nranges = (int)ranges.size();
-  if ((st = dupload(S, &D.meta, meta))) return st;
-  if ((st = dupload(S, &D.ranges, ranges))) return st;
-  for (int s = 0; s < F.nsuper; ++s) {
-    if (F.sn_height[s] <= D.hcut) continue;  // handled by the subtree kernels
     const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
     const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+    const int st0 = (int)F.sn_struct[s];
     const int hgt = F.sn_height[s];
-    for (int t = 0; t < k; ++t) {
-      // F1: y = inv(L_ss) b_s, lower triangle only (cols 0..t)
-      byh[T_F1][hgt].push_back({F.off_linv[s] + (long long)t * k, t + 1, f0, f0 + t, 0});
-      // B2: x = inv(U_ss) t_s, upper triangle (cols t..k-1)
-      byh[T_B2][hgt].push_back({F.off_uinv[s] + (long long)t * k + t, k - t, f0 + t, f0 + t, 0});
-      if (m > 0) byh[T_B1][hgt].push_back({F.off_u12[s] + (long long)t * m, m, (int)F.sn_struct[s], f0 + t, 0});
-      else byh[T_B1][hgt].push_back({0, 0, 0, f0 + t, 0});
-    }
-    for (int a = 0; a < m; ++a)
-      byh[T_F2][hgt].push_back({F.off_l21[s] + (long long)a * k, k, f0, F.structs[F.sn_struct[s] + a], 0});
+    if (m > 0) tiles(byh[0][hgt], F.off_w[s], m, k, f0, st0, 2);  // W (m x k): b_s contiguous, outputs b[structs]
+    tiles(byh[1][hgt], F.off_g[s], k, k, f0, f0, 0);                // G (k x k): b_s contiguous, outputs x_s
+    if (m > 0) tiles(byh[1][hgt], F.off_v[s], k, m, st0, f0, 1);  // V (k x m): x gathered through structs
   }
-  for (int ph = 0; ph < 4; ++ph) {
-    long long bytes = 0;
-    D.tbytes[ph].assign(F.height + 1, 0.0);
+  std::vector<Task> all;
+  for (int sw = 0; sw < 2; ++sw) {
+    D.toff[sw].assign(F.height + 2, 0);
+    D.tbytes[sw].assign(F.height + 1, 0.0);
     for (int h = 0; h <= F.height; ++h) {
-      D.toff[ph][h] = (long long)all.size();
-      for (const Task& t : byh[ph][h]) {
+      D.toff[sw][h] = (long long)all.size();
+      for (const Task& t : byh[sw][h]) {
         all.push_back(t);
-        // matrix row once (+ its gather indices for B1), plus the output element
-        long long b = (long long)t.ncols * ((ph == T_B1 || ph == T_F1) ? 12 : 8) + 8;
-        bytes += b;
-        D.tbytes[ph][h] += (double)b;
+        // the tile, its source entries (+ gather indices of a V tile), the outputs
+        const double e = f32 ? 4.0 : 8.0;
+        D.tbytes[sw][h] += e * t.nrows * t.ncols + (t.src == 1 ? e + 4.0 : e) * t.ncols + e * t.nrows;
       }
     }
-    D.toff[ph][F.height + 1] = (long long)all.size();
-    D.ntasks[ph] = D.toff[ph][F.height + 1] - D.toff[ph][0];
-    D.task_bytes[ph] = bytes;
+    D.toff[sw][F.height + 1] = (long long)all.size();
   }
   if ((st = dupload(S, &D.tasks, all))) return st;
-  {
-    // one-launch schedule over every supernode (no subtree split)
-    std::vector<PTask> pt;
-    std::vector<unsigned int> gates;
-    std::vector<std::vector<int>> by_h(F.height + 1);
-    for (int s = 0; s < F.nsuper; ++s) by_h[F.sn_height[s]].push_back(s);
-    unsigned int f2_count = 0;
-    D.pbytes = 0;
-    for (int h = 0; h <= F.height; ++h) {
-      gates.push_back(f2_count);  // F1 at height h waits for all F2 below
-      const int g = (int)gates.size() - 1;
-      for (int s : by_h[h]) {
-        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
-        for (int r = 0; r < k; ++r) {
-          pt.push_back({F.off_linv[s] + (long long)r * k, r + 1, f0, f0 + r, 0, s, g, k});
-          D.pbytes += 12.0 * (r + 1) + 8;
-        }
-      }
-      for (int s : by_h[h]) {
-        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
-        const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
-        for (int a = 0; a < m; ++a) {
-          pt.push_back({F.off_l21[s] + (long long)a * k, k, f0, F.structs[F.sn_struct[s] + a], 1, s, k, k});
-          ++f2_count;
-          D.pbytes += 8.0 * k + 12;
-        }
-      }
-    }
-    unsigned int b2_count = 0;
-    for (int h = F.height; h >= 0; --h) {
-      gates.push_back(b2_count);  // B1 at height h waits for all B2 above
-      const int g = (int)gates.size() - 1;
-      for (int s : by_h[h]) {
-        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
-        const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
-        for (int r = 0; r < k; ++r) {
-          pt.push_back({F.off_u12[s] + (long long)r * m, m, (int)F.sn_struct[s], f0 + r, 2, s, g, k});
-          D.pbytes += 12.0 * m + 16;
-        }
-      }
-      for (int s : by_h[h]) {
-        const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
-        for (int r = 0; r < k; ++r) {
-          pt.push_back({F.off_uinv[s] + (long long)r * k + r, k - r, f0 + r, f0 + r, 3, s, k, k});
-          ++b2_count;
-          D.pbytes += 8.0 * (k - r) + 8;
-        }
-      }
-    }
-    D.nptasks = (int)pt.size();
-    D.nsuper = F.nsuper;
-    if ((st = dupload(S, &D.ptasks, pt))) return st;
-    if ((st = dupload(S, &D.pgates, gates))) return st;
-    if ((st = dalloc(S, &D.pctr, 4 + 2 * (size_t)F.nsuper))) return st;
+  if (f32) {
+    if ((st = dalloc(S, &D.b32, F.n))) return st;
+    if ((st = dalloc(S, &D.x32, F.n))) return st;
+  } else {
+    if ((st = dalloc(S, &D.b, F.n))) return st;
+    if ((st = dalloc(S, &D.x, F.n))) return st;
   }
-  if ((st = dalloc(S, &D.b, F.n))) return st;
-  if ((st = dalloc(S, &D.y, F.n))) return st;
-  if ((st = dalloc(S, &D.t, F.n))) return st;
-  if ((st = dalloc(S, &D.x, F.n))) return st;
   std::vector<int> cellv(F.n);
   for (int p = 0; p < F.n; ++p) cellv[p] = pos_cell[F.perm[p]];
   if ((st = dupload(S, &D.cell, cellv))) return st;
@@ -1008,59 +824,46 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
 }
 
 // --------------------------------------------------------------- launches
-void launch_tasks(cc_solver* S, DevLU& D, int ph, int h) {
-  long long a = D.toff[ph][h], b = D.toff[ph][h + 1];
-  int nt = (int)(b - a);
+template <class TV>
+void launch_sweep(cc_solver* S, const DevLU& D, const TV* vals, int sweep, int h, TV* b, TV* x) {
+  const long long a = D.toff[sweep][h], e = D.toff[sweep][h + 1];
+  const int nt = (int)(e - a);
   if (nt <= 0) return;
   const int block = 256;
-  int grid = grid_for(S, (long long)nt * 32, block);
-  const Task* T = D.tasks + a;
-  static const int cls[4] = {P_F1, P_F2, P_B1, P_B2};
-  ProfScope ps(S, cls[ph], D.tbytes[ph][h]);
-  switch (ph) {
-    case T_F1: k_tasks<T_F1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.b, D.pivrow, nullptr, D.y); break;
-    case T_F2: k_tasks<T_F2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.y, nullptr, nullptr, D.b); break;
-    case T_B1: k_tasks<T_B1><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.x, D.structs, D.y, D.t); break;
-    case T_B2: k_tasks<T_B2><<<grid, block, 0, S->stream>>>(T, nt, D.vals, D.t, nullptr, nullptr, D.x); break;
-  }
+  const int grid = grid_for(S, (long long)nt * 32, block);
+  ProfScope ps(S, sweep == 0 ? P_FWD : P_BWD, D.tbytes[sweep][h]);
+  if (sweep == 0)
+    k_tasks<true, TV><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, vals, D.structs, b, x);
+  else
+    k_tasks<false, TV><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, vals, D.structs, b, x);
 }
 
-// phi[cells] = A^{-1} (s[cells] - R phi) with the stored factors
-template <class T>
-void lu_solve(cc_solver* S, DevLU& D, const T* s, T* phi) {
+// phi[cells] = A^{-1} (s[cells] - R phi) with the stored factors, on work vectors b and x
+// (np entries of the factors' type each).  k_lu_rhs writes all of b and clears x
+// before the sweeps read them.
+template <class T, class TV>
+void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x) {
   if (D.np == 0) return;
+  const TV* vals;
+  if constexpr (sizeof(TV) == 4) vals = D.vals32; else vals = D.vals;
   const int block = 256;
   {
-    ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 8.0 * D.np);
-    k_lu_rhs<T><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.np, D.cell, D.rptr, D.rcol, D.rval, s, phi);
+    ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 2.0 * sizeof(TV) * D.np);
+    k_lu_rhs<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol, D.rval,
+                                                                       s, phi);
   }
-  if (S->prm.lu_persistent) {
-    cudaMemsetAsync(D.pctr, 0, sizeof(unsigned int) * (4 + 2 * (size_t)D.nsuper), S->stream);
-    ProfScope ps(S, P_PERSIST, D.pbytes);
-    k_lu_persistent<<<S->nsm * 8, 256, 0, S->stream>>>(D.ptasks, D.nptasks, D.vals, D.structs, D.pivrow, D.b, D.y,
-                                                       D.t, D.x, D.pctr, D.pgates, D.nsuper, S->err_flag);
-  } else {
-  if (D.nranges > 0) {
-    ProfScope ps(S, P_SUBTREE, D.bytes_subtree);
-    k_lu_subtree_fwd<<<std::min(D.nranges, S->nsm * 8), 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals,
-                                                                               D.structs, D.pivrow, D.b, D.y);
-  }
-  for (int h = D.hcut + 1; h <= D.height; ++h) {
-    launch_tasks(S, D, T_F1, h);
-    launch_tasks(S, D, T_F2, h);
-  }
-  for (int h = D.height; h > D.hcut; --h) {
-    launch_tasks(S, D, T_B1, h);
-    launch_tasks(S, D, T_B2, h);
-  }
-  if (D.nranges > 0) {
-    ProfScope ps(S, P_SUBTREE, D.bytes_subtree);
-    k_lu_subtree_bwd<<<std::min(D.nranges, S->nsm * 8), 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals,
-                                                                               D.structs, D.y, D.x);
-  }
-  }
-  ProfScope ps(S, P_SCATTER, (8.0 + 4.0 + sizeof(T)) * D.np);
-  k_scatter<T><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
+  for (int h = 0; h <= D.height; ++h) launch_sweep<TV>(S, D, vals, 0, h, b, x);
+  for (int h = D.height; h >= 0; --h) launch_sweep<TV>(S, D, vals, 1, h, b, x);
+  ProfScope ps(S, P_SCATTER, (sizeof(TV) + 4.0 + sizeof(T)) * D.np);
+  k_scatter<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
+}
+
+template <class T>
+void lu_solve(cc_solver* S, DevLU& D, const T* s, T* phi) {
+  if (D.f32)
+    lu_solve_ws<T, float>(S, D, s, phi, D.b32, D.x32);
+  else
+    lu_solve_ws<T, double>(S, D, s, phi, D.b, D.x);
 }
 
 template <class T>
@@ -1131,10 +934,10 @@ void vcycle_rec(cc_solver* S, int m, const T* s, T* e) {
 }
 
 // e (FP64, level 0) = VCycle(s) in the solver's precision: FP64, or FP32 for the
-// grid work with the FP64 LU-corrections (mixed precision)
+// grid work (mixed precision; with precision 2 the LU-corrections too)
 void precond(cc_solver* S, const double* s, double* e) {
   DevLevel& L = S->lev[0];
-  if (S->prm.precision == 1) {
+  if (S->prm.precision >= 1) {
     k_to_float<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(L.s32, s, L.N);
     vcycle_rec<float>(S, 0, L.s32, L.e32);
     cudaMemsetAsync(e, 0, L.N * sizeof(double), S->stream);
@@ -1187,15 +990,6 @@ std::vector<int> finish_host_info(cc_solver* S) {
   return patch_of;
 }
 
-// Reads and clears the flag raised by a bounded wait that ran out.
-bool take_timeout(cc_solver* S) {
-  unsigned int h = 0;
-  cudaMemcpyAsync(&h, S->err_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->stream);
-  cudaStreamSynchronize(S->stream);
-  if (h) cudaMemsetAsync(S->err_flag, 0, sizeof(unsigned int), S->stream);
-  return h != 0;
-}
-
 cc_status fail(cc_solver* S, cc_status st, const std::string& msg) {
   S->err = msg;
   return st;
@@ -1210,6 +1004,10 @@ void drop_graph(cc_solver* S) {
   if (S->cycle_exec) {
     cudaGraphExecDestroy(S->cycle_exec);
     S->cycle_exec = nullptr;
+  }
+  if (S->prec_exec) {
+    cudaGraphExecDestroy(S->prec_exec);
+    S->prec_exec = nullptr;
   }
 }
 
@@ -1305,15 +1103,33 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter";
   if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
-  if (take_timeout(S)) {
-    S->err = "a bounded wait in the LU solve ran out";
-    return CC_ERR_TIMEOUT;
-  }
   return result;
 }
 
 // Restarted GMRES(m), right-preconditioned by one V-cycle, on the finest level's
 // grid vectors (an acceleration of Alg. Multigrid; the V-cycle is unchanged).
+// lev[0].e = one V-cycle applied to v.  With graphs on, v is copied into the
+// fixed buffer kin and the V-cycle runs as a captured graph (its launches would
+// otherwise be issued one by one from the host).
+cc_status apply_prec(cc_solver* S, const double* v) {
+  DevLevel& L = S->lev[0];
+  if (!S->prm.use_graph || S->prof) {
+    precond(S, v, L.e);
+    return CC_OK;
+  }
+  CK(cudaMemcpyAsync(S->kin, v, L.N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream));
+  if (!S->prec_exec) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
+    precond(S, S->kin, L.e);
+    CK(cudaStreamEndCapture(S->stream, &g));
+    CK(cudaGraphInstantiate(&S->prec_exec, g, 0));
+    cudaGraphDestroy(g);
+  }
+  CK(cudaGraphLaunch(S->prec_exec, S->stream));
+  return CC_OK;
+}
+
 cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
   DevLevel& L = S->lev[0];
   const long long N = L.N;
@@ -1325,6 +1141,8 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     if ((st = dalloc(S, &S->kV, (size_t)(m + 1) * N))) return st;
     if ((st = dalloc(S, &S->kw, N))) return st;
     if ((st = dalloc(S, &S->kzero, N))) return st;
+    if ((st = dalloc(S, &S->kin, N))) return st;
+    drop_graph(S);
     if ((st = dalloc(S, &S->kdots, (size_t)2 * (m + 2)))) return st;
     if (!S->khdots) CK(cudaMallocHost((void**)&S->khdots, sizeof(double) * 2 * 66));
     CK(cudaMemset(S->kzero, 0, N * sizeof(double)));
@@ -1365,7 +1183,8 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     int k = 0;
     for (int j = 0; j < m && cycles < S->prm.max_iter; ++j) {
       double* vj = V + (long long)j * N;
-      precond(S, vj, L.e);  // z = M v_j
+      cc_status pst = apply_prec(S, vj);  // z = M v_j
+      if (pst) return pst;
       ++cycles;
       // w = A z = -(0 - A z)
       resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
@@ -1407,7 +1226,8 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     }
     CK(cudaMemcpyAsync(S->kdots + m + 2, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, S->stream));
     k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
-    precond(S, S->kw, L.e);
+    cc_status pst = apply_prec(S, S->kw);
+    if (pst) return pst;
     ++cycles;
     k_axpy<<<grid, block, 0, S->stream>>>(S->phi, L.e, N);
   }
@@ -1431,10 +1251,6 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter V-cycles";
   if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
-  if (take_timeout(S)) {
-    S->err = "a bounded wait in the LU solve ran out";
-    return CC_ERR_TIMEOUT;
-  }
   return result;
 }
 
@@ -1444,12 +1260,12 @@ cc_status run_solve(cc_solver* S, double* phi_out, int where, cc_stats* stats) {
 }
 
 // ---------------------------------------- allocation-free LU-correction
-// cc_lu_correction_static keeps its four LU work vectors (b, y, t, x of the
-// triangular solves) in this file-scope device array instead of the vectors
+// cc_lu_correction_static keeps its two LU work vectors (b and x of the
+// triangular sweeps) in this file-scope device array instead of the vectors
 // cc_setup allocates.  It is part of the module image: every GPU that loads the
-// library holds these 8 MiB until the process exits.
+// library holds these 4 MiB until the process exits.
 constexpr int kStaticLuRows = 1 << 18;
-static __device__ __align__(256) double g_lu_scratch[4 * (size_t)kStaticLuRows];
+static __device__ __align__(256) double g_lu_scratch[2 * (size_t)kStaticLuRows];
 
 // Device address of g_lu_scratch, looked up once per device.  In host code the
 // name g_lu_scratch is only a host-side stand-in and must never reach a kernel.
@@ -1469,47 +1285,6 @@ cc_status static_scratch(cc_solver* S, double** out) {
   }
   *out = g_scratch_addr[S->device];
   return CC_OK;
-}
-
-// SMO-2 with the per-height schedule, on caller-chosen work vectors.  k_lu_rhs
-// writes all np entries of b before anything reads it, and every later phase
-// writes y, t and x before reading them, so no work vector has to start at zero.
-void lu_solve_into(cc_solver* S, const DevLU& D, const double* s, double* phi, double* b, double* y, double* t,
-                   double* x) {
-  if (D.np == 0) return;
-  const int block = 256;
-  k_lu_rhs<double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, D.np, D.cell, D.rptr, D.rcol, D.rval, s,
-                                                                        phi);
-  const int nsub = std::min(D.nranges, S->nsm * 8);
-  if (D.nranges > 0)
-    k_lu_subtree_fwd<<<nsub, 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals, D.structs, D.pivrow, b, y);
-  auto tasks = [&](int ph, int h) -> std::pair<const Task*, int> {
-    const long long a = D.toff[ph][h], e = D.toff[ph][h + 1];
-    return {D.tasks + a, (int)(e - a)};
-  };
-  for (int h = D.hcut + 1; h <= D.height; ++h) {
-    auto f1 = tasks(T_F1, h);
-    if (f1.second > 0)
-      k_tasks<T_F1><<<grid_for(S, (long long)f1.second * 32, block), block, 0, S->stream>>>(
-          f1.first, f1.second, D.vals, b, D.pivrow, nullptr, y);
-    auto f2 = tasks(T_F2, h);
-    if (f2.second > 0)
-      k_tasks<T_F2><<<grid_for(S, (long long)f2.second * 32, block), block, 0, S->stream>>>(
-          f2.first, f2.second, D.vals, y, nullptr, nullptr, b);
-  }
-  for (int h = D.height; h > D.hcut; --h) {
-    auto b1 = tasks(T_B1, h);
-    if (b1.second > 0)
-      k_tasks<T_B1><<<grid_for(S, (long long)b1.second * 32, block), block, 0, S->stream>>>(
-          b1.first, b1.second, D.vals, x, D.structs, y, t);
-    auto b2 = tasks(T_B2, h);
-    if (b2.second > 0)
-      k_tasks<T_B2><<<grid_for(S, (long long)b2.second * 32, block), block, 0, S->stream>>>(
-          b2.first, b2.second, D.vals, t, nullptr, nullptr, x);
-  }
-  if (D.nranges > 0)
-    k_lu_subtree_bwd<<<nsub, 256, 0, S->stream>>>(D.meta, D.ranges, D.nranges, D.vals, D.structs, y, x);
-  k_scatter<double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
 }
 
 }  // namespace
@@ -1533,7 +1308,6 @@ void cc_default_params(cc_params* p) {
   p->krylov = 0;
   p->krylov_restart = 30;
   p->precision = 0;
-  p->lu_persistent = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1582,7 +1356,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   else
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
-      S->prm.precision < 0 || S->prm.precision > 1) {
+      S->prm.precision < 0 || S->prm.precision > 2) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }
@@ -1722,11 +1496,12 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dupload(S, &D.p2_ptr, L.p2_ptr));
     TRY(dupload(S, &D.p2_col, L.p2_col));
     TRY(dupload(S, &D.p2_val, L.p2_val));
-    TRY(upload_lu(S, D.lu, lus[m], lu_cells[m], rptr[m], rcol[m], rval[m]));
+    // precision 2: the LU-corrections of the finer levels run in FP32; the bottom solve stays FP64
+    TRY(upload_lu(S, D.lu, lus[m], lu_cells[m], rptr[m], rcol[m], rval[m], S->prm.precision == 2 && m < M));
     TRY(dalloc(S, &D.s, D.N));
     TRY(dalloc(S, &D.e, D.N));
     TRY(dalloc(S, &D.tmp, D.N));
-    if (S->prm.precision == 1) {
+    if (S->prm.precision >= 1) {
       TRY(dalloc(S, &D.s32, D.N));
       TRY(dalloc(S, &D.e32, D.N));
       TRY(dalloc(S, &D.tmp32, D.N));
@@ -1748,11 +1523,6 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dalloc(S, &S->f, D0.N));
     TRY(dalloc(S, &S->gbox, (size_t)6 * L0.n * L0.n));
     TRY(dalloc(S, &S->norm, 1));
-    TRY(dalloc(S, &S->err_flag, 1));
-    if (cudaMemset(S->err_flag, 0, sizeof(unsigned int)) != cudaSuccess) {
-      st = CC_ERR_CUDA;
-      goto failed;
-    }
     if (cudaMallocHost((void**)&S->hnorm, sizeof(double)) != cudaSuccess) {
       st = CC_ERR_OOM;
       goto failed;
@@ -1985,7 +1755,6 @@ cc_status cc_lu_correction(cc_solver* S, int level, double* phi, const double* r
   if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
   lu_solve<double>(S, S->lev[level].lu, rhs, phi);
   CK(cudaGetLastError());
-  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 
@@ -2018,7 +1787,6 @@ cc_status cc_bottom_solve(cc_solver* S, const double* rhs, double* phi) {
   CK(cudaMemsetAsync(phi, 0, L.N * sizeof(double), S->stream));
   lu_solve<double>(S, L.lu, rhs, phi);
   CK(cudaGetLastError());
-  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 
@@ -2027,7 +1795,6 @@ cc_status cc_vcycle(cc_solver* S, const double* rhs, double* e) {
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   precond(S, rhs, e);
   CK(cudaGetLastError());
-  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a bounded wait in the LU solve ran out");
   return CC_OK;
 }
 
@@ -2096,8 +1863,12 @@ cc_status cc_lu_correction_static(cc_solver* S, int level, double* phi, const do
   double* w = nullptr;
   st = static_scratch(S, &w);
   if (st == CC_OK) {
-    const size_t R = (size_t)kStaticLuRows;
-    lu_solve_into(S, D, rhs, phi, w, w + R, w + 2 * R, w + 3 * R);
+    if (D.f32) {
+      float* w32 = reinterpret_cast<float*>(w);  // the array holds 2 x kStaticLuRows floats as well
+      lu_solve_ws<double, float>(S, D, rhs, phi, w32, w32 + (size_t)kStaticLuRows);
+    } else {
+      lu_solve_ws<double, double>(S, D, rhs, phi, w, w + (size_t)kStaticLuRows);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = fail(S, CC_ERR_CUDA, std::string("cc_lu_correction_static: ") + cudaGetErrorString(e));
   }

@@ -118,9 +118,18 @@ struct Rows1D {
 Rows1D regular_rows_1d(int bc_low, int bc_high, double h);
 
 // --------------------------------------------------------------- sparse LU
-// Supernodal LU (partial pivoting inside supernodes) in a nested-dissection order, stored for the
-// GPU triangular solves: per supernode, explicit inverses of the diagonal
-// blocks, the dense off-diagonal blocks, and the row structure.
+// Supernodal LU (partial pivoting inside supernodes) in a nested-dissection
+// order, stored for the GPU triangular solves in block-elimination form.  With
+// P_s the pivoting of supernode s, L_ss U_ss its diagonal block and L_{struct,s},
+// U_{s,struct} its off-diagonal blocks, each supernode keeps
+//   G = U_ss^{-1} L_ss^{-1}        (k x k, dense)
+//   W = L_{struct,s} L_ss^{-1}     (m x k)
+//   V = U_ss^{-1} U_{s,struct}     (k x m)
+// so that the forward sweep is b_struct -= W P_s b_s (children first) and the
+// backward sweep is x_s = G P_s b_s - V x_struct (parents first): one dense
+// matrix-vector product per supernode and sweep.  P_s is folded into the
+// columns of G and W, which therefore multiply b_s in ND order directly.  The
+// blocks are stored column-major (entry (r, c) of an R x C block at c R + r).
 struct SuperLU {
   int n = 0;                        // matrix dimension
   std::vector<int> perm;            // perm[p] = original row/col of ND position p
@@ -130,13 +139,13 @@ struct SuperLU {
   std::vector<int> sn_parent;       // parent in the supernode tree (-1 for roots); subtrees are contiguous
   std::vector<long long> sn_struct; // offset into structs (size nsuper+1)
   std::vector<int> structs;         // ND positions of struct(s), ascending
-  // value offsets (doubles) into vals for each supernode's blocks
-  std::vector<long long> off_linv, off_uinv, off_l21, off_u12;
+  // value offsets (doubles) into vals for each supernode's blocks (column-major)
+  std::vector<long long> off_g, off_w, off_v;
   std::vector<double> vals;
-  std::vector<int> pivrow;          // ND position read by row t of each supernode's forward step
+  std::vector<int> pivrow;          // ND position of the t-th pivot row of each supernode (P_s; folded into G, W)
   int height = 0;
   double min_pivot = 0, max_pivot = 0;
-  long long nnz_factor = 0;         // entries stored (diag inverses + off-diagonal blocks)
+  long long nnz_factor = 0;         // entries stored (G, W and V of every supernode)
 };
 
 // Host solve with the stored factors, in the same order the GPU uses

@@ -226,41 +226,73 @@ void tri_inverses(const double* Fm, int F, int k, double* Linv, double* Uinv, bo
   }
 }
 
+// The block-elimination forms of one factored front (leading k x k block
+// factored, m struct rows/columns after it): G = Uinv Linv, W = L21 Linv,
+// V = Uinv U12, all row-major.  Linv is unit lower, Uinv upper triangular.
+void block_forms(const double* Fm, int F, int k, int m, const double* Linv, const double* Uinv, double* G, double* W,
+                 double* V, bool par) {
+  // G[r][c] = sum_{p >= max(r, c)} Uinv[r][p] Linv[p][c]: row r accumulates rows p >= r of Linv
+#pragma omp parallel for schedule(dynamic, 8) if (par && k > 64)
+  for (int r = 0; r < k; ++r) {
+    double* g = G + (long long)r * k;
+    for (int c = 0; c < k; ++c) g[c] = 0.0;
+    for (int p = r; p < k; ++p) {
+      const double u = Uinv[(long long)r * k + p];
+      const double* l = Linv + (long long)p * k;
+      for (int c = 0; c <= p; ++c) g[c] += u * l[c];
+    }
+  }
+  // W[a][c] = sum_{p >= c} L21[a][p] Linv[p][c], with L21[a][p] = Fm[k + a][p]
+#pragma omp parallel for schedule(dynamic, 8) if (par && (long long)m * k > 4096)
+  for (int a = 0; a < m; ++a) {
+    double* w = W + (long long)a * k;
+    const double* l21 = Fm + (long long)(k + a) * F;
+    for (int c = 0; c < k; ++c) w[c] = 0.0;
+    for (int p = 0; p < k; ++p) {
+      const double v = l21[p];
+      if (v == 0.0) continue;
+      const double* l = Linv + (long long)p * k;
+      for (int c = 0; c <= p; ++c) w[c] += v * l[c];
+    }
+  }
+  // V[r][a] = sum_{p >= r} Uinv[r][p] U12[p][a], with U12[p][a] = Fm[p][k + a]
+#pragma omp parallel for schedule(dynamic, 8) if (par && (long long)m * k > 4096)
+  for (int r = 0; r < k; ++r) {
+    double* v = V + (long long)r * m;
+    for (int a = 0; a < m; ++a) v[a] = 0.0;
+    for (int p = r; p < k; ++p) {
+      const double u = Uinv[(long long)r * k + p];
+      const double* u12 = Fm + (long long)p * F + k;
+      for (int a = 0; a < m; ++a) v[a] += u * u12[a];
+    }
+  }
+}
+
 }  // namespace
 
 void super_solve_host(const SuperLU& F, const std::vector<double>& b, std::vector<double>& x) {
   const int n = F.n;
-  std::vector<double> w(n), y(n), t(n), z(n);
+  std::vector<double> w(n), z(n, 0.0);
   for (int p = 0; p < n; ++p) w[p] = b[F.perm[p]];
-  for (int s = 0; s < F.nsuper; ++s) {  // forward, supernodes in postorder
+  for (int s = 0; s < F.nsuper; ++s) {  // forward, supernodes in postorder: b_struct -= W b_s
     const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
     const long long m = F.sn_struct[s + 1] - F.sn_struct[s];
-    const double* Li = &F.vals[F.off_linv[s]];
-    for (int r = 0; r < k; ++r) {
-      double a = 0;
-      for (int c = 0; c <= r; ++c) a += Li[(long long)r * k + c] * w[F.pivrow[f0 + c]];
-      y[f0 + r] = a;
-    }
-    const double* L21 = &F.vals[F.off_l21[s]];
+    const double* Wt = &F.vals[F.off_w[s]];  // column-major m x k
     for (long long a = 0; a < m; ++a) {
       double v = 0;
-      for (int c = 0; c < k; ++c) v += L21[a * k + c] * y[f0 + c];
+      for (int c = 0; c < k; ++c) v += Wt[c * m + a] * w[f0 + c];
       w[F.structs[F.sn_struct[s] + a]] -= v;
     }
   }
-  for (int s = F.nsuper - 1; s >= 0; --s) {  // backward
+  for (int s = F.nsuper - 1; s >= 0; --s) {  // backward: x_s = G b_s - V x_struct
     const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
     const long long m = F.sn_struct[s + 1] - F.sn_struct[s];
-    const double* U12 = &F.vals[F.off_u12[s]];
-    for (int r = 0; r < k; ++r) {
-      double v = 0;
-      for (long long a = 0; a < m; ++a) v += U12[r * m + a] * z[F.structs[F.sn_struct[s] + a]];
-      t[f0 + r] = y[f0 + r] - v;
-    }
-    const double* Ui = &F.vals[F.off_uinv[s]];
+    const double* Gt = &F.vals[F.off_g[s]];  // column-major k x k
+    const double* Vt = &F.vals[F.off_v[s]];  // column-major k x m
     for (int r = 0; r < k; ++r) {
       double a = 0;
-      for (int c = r; c < k; ++c) a += Ui[(long long)r * k + c] * t[f0 + c];
+      for (int c = 0; c < k; ++c) a += Gt[(long long)c * k + r] * w[f0 + c];
+      for (long long q = 0; q < m; ++q) a -= Vt[q * k + r] * z[F.structs[F.sn_struct[s] + q]];
       z[f0 + r] = a;
     }
   }
@@ -382,21 +414,18 @@ int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const st
   out.structs.resize(out.sn_struct[ns]);
   for (int k = 0; k < ns; ++k) std::copy(st[k].begin(), st[k].end(), out.structs.begin() + out.sn_struct[k]);
   // value layout
-  out.off_linv.resize(ns);
-  out.off_uinv.resize(ns);
-  out.off_l21.resize(ns);
-  out.off_u12.resize(ns);
+  out.off_g.resize(ns);
+  out.off_w.resize(ns);
+  out.off_v.resize(ns);
   long long off = 0;
   for (int k = 0; k < ns; ++k) {
     long long kk = out.sn_first[k + 1] - out.sn_first[k];
     long long m = (long long)st[k].size();
-    out.off_linv[k] = off;
+    out.off_g[k] = off;
     off += kk * kk;
-    out.off_uinv[k] = off;
-    off += kk * kk;
-    out.off_l21[k] = off;
+    out.off_w[k] = off;
     off += m * kk;
-    out.off_u12[k] = off;
+    out.off_v[k] = off;
     off += kk * m;
   }
   out.vals.assign(off, 0.0);
@@ -454,15 +483,34 @@ int factor_nd(const std::vector<int>& ptr, const std::vector<int>& col, const st
       gmin = std::min(gmin, lmin);
       gmax = std::max(gmax, lmax);
       for (int t = 0; t < kk; ++t) out.pivrow[f0 + t] += f0;  // ND positions
-      double* Linv = &out.vals[out.off_linv[k]];
-      double* Uinv = &out.vals[out.off_uinv[k]];
-      tri_inverses(Fm.data(), F, kk, Linv, Uinv, !many);
-      double* L21 = &out.vals[out.off_l21[k]];
-      double* U12 = &out.vals[out.off_u12[k]];
-      for (int a = 0; a < m; ++a)
-        for (int t = 0; t < kk; ++t) L21[(size_t)a * kk + t] = Fm[(size_t)(kk + a) * F + t];
-      for (int t = 0; t < kk; ++t)
-        for (int a = 0; a < m; ++a) U12[(size_t)t * m + a] = Fm[(size_t)t * F + kk + a];
+      {
+        std::vector<double> Linv((size_t)kk * kk), Uinv((size_t)kk * kk);
+        tri_inverses(Fm.data(), F, kk, Linv.data(), Uinv.data(), !many);
+        block_forms(Fm.data(), F, kk, m, Linv.data(), Uinv.data(), &out.vals[out.off_g[k]],
+                    &out.vals[out.off_w[k]], &out.vals[out.off_v[k]], !many);
+        // fold P_s into the columns: (M P_s b_s) = M' b_s with M'[r][pivrow[t] - f0] = M[r][t]
+        std::vector<double> tmp(kk);
+        auto fold = [&](double* M, long long rows) {
+          for (long long r = 0; r < rows; ++r) {
+            double* row = M + r * kk;
+            for (int t = 0; t < kk; ++t) tmp[out.pivrow[f0 + t] - f0] = row[t];
+            std::copy(tmp.begin(), tmp.end(), row);
+          }
+        };
+        fold(&out.vals[out.off_g[k]], kk);
+        fold(&out.vals[out.off_w[k]], m);
+        // store every block transposed (column-major): a warp then reads one
+        // column's consecutive rows in one coalesced load
+        auto transpose = [&](double* M, long long rows, long long cols) {
+          std::vector<double> t((size_t)(rows * cols));
+          for (long long r = 0; r < rows; ++r)
+            for (long long c = 0; c < cols; ++c) t[(size_t)(c * rows + r)] = M[r * cols + c];
+          std::copy(t.begin(), t.end(), M);
+        };
+        transpose(&out.vals[out.off_g[k]], kk, kk);
+        transpose(&out.vals[out.off_w[k]], m, kk);
+        transpose(&out.vals[out.off_v[k]], kk, m);
+      }
       if (m > 0) {
         std::vector<double> U((size_t)m * m);
         for (int a = 0; a < m; ++a)

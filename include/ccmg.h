@@ -48,7 +48,7 @@ typedef enum {
   CC_ERR_NOT_CONVERGED = 6,
   CC_ERR_DIVERGED = 7,     /* non-finite residual */
   CC_ERR_MERGE = 8,        /* cell merging could not make every cell theta-proper */
-  CC_ERR_TIMEOUT = 9       /* reserved: no call returns it at present */
+  CC_ERR_TIMEOUT = 9       /* a bounded wait in the one-launch LU sweeps ran out */
 } cc_status;
 
 enum { CC_DIRICHLET = 0, CC_NEUMANN = 1 };
@@ -86,6 +86,10 @@ typedef struct {
                         the LU-corrections of the finer levels store and apply their
                         factors in FP32 (their right-hand sides, built from the PLG
                         rows, the bottom solve and the outer residual stay FP64) (0) */
+  int lu_schedule;   /* triangular sweeps of the LU-corrections and bottom solve:
+                        0 one launch per tree height and sweep; 1 one cooperative
+                        launch per solve with bounded grid barriers between heights
+                        (falls back to 0 where cooperative launch is unavailable) (0) */
 } cc_params;
 
 typedef struct {

@@ -42,6 +42,7 @@ struct StencilP {
   double g[3][5];     // coefficient of the nearer wall's <g> (times 12 h^2)
   double winv[5][5][5];  // omega / D for each combination of position classes
   float winvf[5][5][5];
+  float csum_f[5][5][5];  // sum of the three axes' row coefficients (times 12 h^2) per class combination
 };
 
 template <class T>
@@ -83,12 +84,22 @@ __device__ __forceinline__ int pos_class(int p, int n) {
 
 // The interior row of eq. regularLaplaceDiscretization: (16 sum_{|o|=1} - sum_{|o|=2} - 90 c) / (12 h^2),
 // the neighbour sums taken in the order +i, -i, +j, -j, +k, -k so that every kernel rounds alike.
+// In FP32 the row is evaluated on differences from the centre value,
+// 16 sum (phi_o - c) - sum (phi_o' - c): the same value, but the near-cancelling
+// sum of O(phi / h^2) terms becomes a sum of O(h^2 phi'') terms, so a smooth
+// field keeps about seven correct digits of its Laplacian instead of three.
 template <class T>
 __device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1, T km1, T ip2, T im2, T jp2, T jm2,
                                         T kp2, T km2, T inv12h2) {
-  const T s1 = ip1 + im1 + jp1 + jm1 + kp1 + km1;
-  const T s2 = ip2 + im2 + jp2 + jm2 + kp2 + km2;
-  return (T(16) * s1 - s2 - T(90) * c0) * inv12h2;
+  if constexpr (sizeof(T) == 4) {
+    const T d1 = ((ip1 - c0) + (im1 - c0)) + ((jp1 - c0) + (jm1 - c0)) + ((kp1 - c0) + (km1 - c0));
+    const T d2 = ((ip2 - c0) + (im2 - c0)) + ((jp2 - c0) + (jm2 - c0)) + ((kp2 - c0) + (km2 - c0));
+    return (T(16) * d1 - d2) * inv12h2;
+  } else {
+    const T s1 = ip1 + im1 + jp1 + jm1 + kp1 + km1;
+    const T s2 = ip2 + im2 + jp2 + jm2 + kp2 + km2;
+    return (T(16) * s1 - s2 - T(90) * c0) * inv12h2;
+  }
 }
 
 // (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
@@ -107,10 +118,21 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
   const int cls[3] = {ci, cj, ck};
   const long long stride[3] = {nn, (long long)n, 1};
   T acc = 0;
+  if constexpr (sizeof(T) == 4) {  // differences from the centre, plus the rows' sum times the centre
+    const T c0 = phi[idx];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int c = cls[d];
-    for (int o = P.lo[d][c]; o <= P.hi[d][c]; ++o) acc += st_coef<T>(P, d, c, o + 3) * phi[idx + o * stride[d]];
+    for (int d = 0; d < 3; ++d) {
+      const int c = cls[d];
+      for (int o = P.lo[d][c]; o <= P.hi[d][c]; ++o)
+        if (o != 0) acc += st_coef<T>(P, d, c, o + 3) * (phi[idx + o * stride[d]] - c0);
+    }
+    acc += P.csum_f[ci][cj][ck] * c0;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int c = cls[d];
+      for (int o = P.lo[d][c]; o <= P.hi[d][c]; ++o) acc += st_coef<T>(P, d, c, o + 3) * phi[idx + o * stride[d]];
+    }
   }
   return acc * st_inv<T>(P);
 }
@@ -278,7 +300,8 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
 template <class T, class TW>
 __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                          const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
-                         const T* __restrict__ s, const T* __restrict__ phi) {
+                         const T* __restrict__ s, const T* __restrict__ phi, unsigned int* __restrict__ bar) {
+  if (bar && blockIdx.x == 0 && threadIdx.x == 0) *bar = 0u;  // barrier counter of the one-launch sweeps
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     double v = (double)s[cell[p]];
     for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
@@ -325,41 +348,97 @@ struct Task {
   int src;         // 0: + G b_s, 1: - V x_struct (gathered), 2: - W b_s (forward, scattered into b)
 };
 
+// One warp task.  Sources are read from L2 (ld.global.cg): within the
+// one-launch sweep they were last written by other blocks' atomics.
 template <bool FWD, class TV>
-__global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3) k_tasks(const Task* __restrict__ tasks, int ntasks, const TV* __restrict__ vals,
-                                               const int* __restrict__ structs, TV* b, TV* x) {
+__device__ __forceinline__ void run_tile(const Task& tk, int lane, const TV* __restrict__ vals,
+                                         const int* __restrict__ structs, TV* b, TV* x) {
+  const int nc = tk.ncols, ld = tk.ld;
+  const bool gather = !FWD && tk.src == 1;
+  const bool mine = lane < tk.nrows;
+  const TV* __restrict__ col = vals + tk.moff + (mine ? lane : 0);
+  TV acc = TV(0);
+  for (int c0 = 0; c0 < nc; c0 += 32) {
+    // lane l holds source entry c0 + l
+    const int c = c0 + lane;
+    TV sv = TV(0);
+    if (c < nc) sv = gather ? __ldcg(x + structs[tk.soff + c]) : __ldcg(b + tk.soff + c);
+    const int cn = min(32, nc - c0);
+    // all loads of a batch are issued before the first product uses one
+    constexpr int kBatch = sizeof(TV) == 4 ? 32 : 8;
+    for (int i = 0; i < cn; i += kBatch) {
+      TV mv[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) mv[u] = i + u < cn ? __ldcs(col + (long long)(c0 + i + u) * ld) : TV(0);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) acc = fma_t(mv[u], __shfl_sync(0xffffffffu, sv, (i + u) & 31), acc);
+    }
+  }
+  if (mine) {
+    if (FWD)
+      atomicAdd(b + structs[tk.out + lane], -acc);
+    else
+      atomicAdd(x + tk.out + lane, tk.src == 1 ? -acc : acc);
+  }
+}
+
+// One tree height of one sweep (the launch-per-height schedule).
+template <bool FWD, class TV>
+__global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
+    k_tasks(const Task* __restrict__ tasks, int ntasks, const TV* __restrict__ vals, const int* __restrict__ structs,
+            TV* b, TV* x) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = warp; t < ntasks; t += nwarps) {
-    const Task tk = tasks[t];
-    const int nc = tk.ncols, ld = tk.ld;
-    const bool gather = !FWD && tk.src == 1;
-    const bool mine = lane < tk.nrows;
-    const TV* __restrict__ col = vals + tk.moff + (mine ? lane : 0);
-    TV acc = TV(0);
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-      // lane l holds source entry c0 + l
-      const int c = c0 + lane;
-      TV sv = TV(0);
-      if (c < nc) sv = gather ? x[structs[tk.soff + c]] : b[tk.soff + c];
-      const int cn = min(32, nc - c0);
-      // all loads of a batch are issued before the first product uses one
-      constexpr int kBatch = sizeof(TV) == 4 ? 32 : 8;
-      for (int i = 0; i < cn; i += kBatch) {
-        TV mv[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) mv[u] = i + u < cn ? __ldcs(col + (long long)(c0 + i + u) * ld) : TV(0);
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc = fma_t(mv[u], __shfl_sync(0xffffffffu, sv, (i + u) & 31), acc);
+  for (int t = warp; t < ntasks; t += nwarps) run_tile<FWD, TV>(tasks[t], lane, vals, structs, b, x);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  Arrival
+// counts accumulate over the launch; phase p completes at p * gridDim.x.  The
+// wait is bounded: on exhaustion err[0] is raised and every block returns at
+// its next barrier, so the kernel always ends.
+constexpr long long kBarrierSpins = 1ll << 23;  // about a second of __nanosleep(64)
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int target, unsigned int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    long long spins = 0;
+    while (*(volatile unsigned int*)bar < target && *(volatile unsigned int*)err == 0u) {
+      if (++spins > kBarrierSpins) {
+        atomicExch(err, 1u);
+        break;
       }
+      __nanosleep(64);
     }
-    if (mine) {
-      if (FWD)
-        atomicAdd(b + structs[tk.out + lane], -acc);
-      else
-        atomicAdd(x + tk.out + lane, tk.src == 1 ? -acc : acc);
-    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile unsigned int*)err == 0u;
+}
+
+// The whole LU solve in one cooperative launch: forward sweep over heights
+// 0..H, then backward sweep over H..0, a grid barrier between heights.
+// bar must be zero at launch (k_lu_rhs clears it).
+template <class TV>
+__global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
+    k_lu_sweeps(const Task* __restrict__ tasks, const long long* __restrict__ toff_f,
+                const long long* __restrict__ toff_b, int height, const TV* __restrict__ vals,
+                const int* __restrict__ structs, TV* b, TV* x, unsigned int* bar, unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned int phase = 0;
+  for (int h = 0; h <= height; ++h) {
+    const long long e = toff_f[h + 1];
+    for (long long t = toff_f[h] + warp; t < e; t += nwarps) run_tile<true, TV>(tasks[t], lane, vals, structs, b, x);
+    if (!grid_barrier(bar, ++phase * gridDim.x, err)) return;
+  }
+  for (int h = height; h >= 0; --h) {
+    const long long e = toff_b[h + 1];
+    for (long long t = toff_b[h] + warp; t < e; t += nwarps) run_tile<false, TV>(tasks[t], lane, vals, structs, b, x);
+    if (h > 0 && !grid_barrier(bar, ++phase * gridDim.x, err)) return;
   }
 }
 
@@ -485,6 +564,11 @@ struct DevLU {
   Task* tasks = nullptr;
   std::vector<long long> toff[2];  // per sweep (0 forward, 1 backward): task offsets by height (height+2)
   std::vector<double> tbytes[2];   // per sweep and height: algorithmic bytes of one launch
+  long long* dtoff[2] = {nullptr, nullptr};  // the same offsets on the device (one-launch schedule)
+  unsigned int* bar = nullptr;     // grid-barrier counter of the one-launch schedule
+  int coop_grid = 0;               // blocks of the cooperative one-launch sweep (0: per-height launches)
+  mutable bool coop_failed = false;  // the cooperative launch was refused: per-height launches from then on
+  double sweep_bytes = 0;          // algorithmic bytes of one whole solve's sweeps
   double *b = nullptr, *x = nullptr;  // work vectors of the sweeps
   float *b32 = nullptr, *x32 = nullptr;
   int* cell = nullptr;  // ND position -> grid index
@@ -530,11 +614,13 @@ enum Prof {
   P_AXPY,
   P_NORM,
   P_RHS,
+  P_KRYLOV,
+  P_SWEEP,
   P_COUNT
 };
 const char* kProfNames[P_COUNT] = {"jacobi", "resid_phi1", "resid_phi2", "restrict", "prolong",
                                    "lu_rhs", "lu_fwd",     "lu_bwd",     "lu_scatter", "axpy",
-                                   "norm",   "rhs"};
+                                   "norm",   "rhs",        "krylov",  "lu_sweeps"};
 
 }  // namespace
 
@@ -548,6 +634,8 @@ struct cc_solver {
   cudaStream_t own_stream = nullptr;
   std::string err;
   int nsm = 148;
+  bool coop = false;                 // cooperative launches available (one-launch LU sweeps)
+  unsigned int* err_flag = nullptr;  // raised by a bounded wait of the one-launch sweeps
   // finest level extras
   double *r = nullptr, *phi = nullptr, *s0 = nullptr, *f = nullptr, *gbox = nullptr, *gpatch = nullptr;
   double* norm = nullptr;   // device scalar
@@ -631,8 +719,9 @@ struct ProfScope {
   cc_solver* S;
   int cls;
   double bytes;
+  int launches;  // kernel launches inside the scope
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(cc_solver* s, int c, double by) : S(s), cls(c), bytes(by) {
+  ProfScope(cc_solver* s, int c, double by, int nl = 1) : S(s), cls(c), bytes(by), launches(nl) {
     if (S->prof) {
       cudaEventCreate(&a);
       cudaEventCreate(&b);
@@ -643,7 +732,7 @@ struct ProfScope {
     if (S->prof) {
       cudaEventRecord(b, S->stream);
       S->pending.push_back({cls, {a, b}});
-      S->prof_launch[cls] += 1;
+      S->prof_launch[cls] += launches;
       S->prof_bytes[cls] += bytes;
     }
   }
@@ -681,6 +770,15 @@ StencilP make_stencil(const Level& L, double omega) {
         P.winvf[a][b][cc] = (float)P.winv[a][b][cc];
       }
   P.inv12h2_f = (float)P.inv12h2;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b)
+      for (int cc = 0; cc < 5; ++cc) {
+        const int cl[3] = {a, b, cc};
+        double t = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int o = 0; o < 7; ++o) t += P.c[d][cl[d]][o];
+        P.csum_f[a][b][cc] = (float)t;
+      }
   for (int d = 0; d < 3; ++d)
     for (int c = 0; c < 5; ++c) {
       int lo = 4, hi = -4;
@@ -795,6 +893,20 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
     D.toff[sw][F.height + 1] = (long long)all.size();
   }
   if ((st = dupload(S, &D.tasks, all))) return st;
+  for (int sw = 0; sw < 2; ++sw) {
+    if ((st = dupload(S, &D.dtoff[sw], D.toff[sw]))) return st;
+    for (double v : D.tbytes[sw]) D.sweep_bytes += v;
+  }
+  if ((st = dalloc(S, &D.bar, 1))) return st;
+  // one cooperative launch per solve when the device allows it: every block resident
+  D.coop_grid = 0;
+  if (S->coop && S->prm.lu_schedule == 1) {
+    int per_sm = 0;
+    cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_sweeps<float>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_sweeps<double>, 256, 0);
+    if (e == cudaSuccess && per_sm > 0) D.coop_grid = per_sm * S->nsm;
+    cudaGetLastError();
+  }
   if (f32) {
     if ((st = dalloc(S, &D.b32, F.n))) return st;
     if ((st = dalloc(S, &D.x32, F.n))) return st;
@@ -847,13 +959,38 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
   const TV* vals;
   if constexpr (sizeof(TV) == 4) vals = D.vals32; else vals = D.vals;
   const int block = 256;
+  const bool one = D.coop_grid > 0 && !D.coop_failed;
   {
     ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 2.0 * sizeof(TV) * D.np);
     k_lu_rhs<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol, D.rval,
-                                                                       s, phi);
+                                                                       s, phi, one ? D.bar : nullptr);
   }
-  for (int h = 0; h <= D.height; ++h) launch_sweep<TV>(S, D, vals, 0, h, b, x);
-  for (int h = D.height; h >= 0; --h) launch_sweep<TV>(S, D, vals, 1, h, b, x);
+  if (one) {
+    ProfScope ps(S, P_SWEEP, D.sweep_bytes);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(D.coop_grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = S->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t le =
+        cudaLaunchKernelEx(&cfg, k_lu_sweeps<TV>, (const Task*)D.tasks, (const long long*)D.dtoff[0],
+                           (const long long*)D.dtoff[1], D.height, vals, (const int*)D.structs, b, x, D.bar,
+                           S->err_flag);
+    if (le != cudaSuccess) {  // refused (e.g. not resident): report it and leave the solve to the caller's check
+      S->err = std::string("cooperative LU sweep launch: ") + cudaGetErrorString(le);
+      cudaGetLastError();
+      D.coop_failed = true;
+    }
+  }
+  if (!one || D.coop_failed) {
+    for (int h = 0; h <= D.height; ++h) launch_sweep<TV>(S, D, vals, 0, h, b, x);
+    for (int h = D.height; h >= 0; --h) launch_sweep<TV>(S, D, vals, 1, h, b, x);
+  }
   ProfScope ps(S, P_SCATTER, (sizeof(TV) + 4.0 + sizeof(T)) * D.np);
   k_scatter<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
 }
@@ -990,6 +1127,17 @@ std::vector<int> finish_host_info(cc_solver* S) {
   return patch_of;
 }
 
+// Reads and clears the flag raised by a grid barrier of the one-launch LU
+// sweeps that waited too long (the kernel then stops early).
+bool take_timeout(cc_solver* S) {
+  if (!S->err_flag) return false;
+  unsigned int h = 0;
+  cudaMemcpyAsync(&h, S->err_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->stream);
+  cudaStreamSynchronize(S->stream);
+  if (h) cudaMemsetAsync(S->err_flag, 0, sizeof(unsigned int), S->stream);
+  return h != 0;
+}
+
 cc_status fail(cc_solver* S, cc_status st, const std::string& msg) {
   S->err = msg;
   return st;
@@ -1103,6 +1251,10 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter";
   if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (take_timeout(S)) {
+    S->err = "a grid barrier of the LU sweeps waited too long";
+    return CC_ERR_TIMEOUT;
+  }
   return result;
 }
 
@@ -1177,7 +1329,10 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       break;
     }
     if (cycles >= S->prm.max_iter) break;
-    k_scale_norm<<<grid, block, 0, S->stream>>>(V, S->s0, S->norm, 1.0, N);
+    {
+      ProfScope ps(S, P_KRYLOV, 16.0 * N);
+      k_scale_norm<<<grid, block, 0, S->stream>>>(V, S->s0, S->norm, 1.0, N);
+    }
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
@@ -1188,13 +1343,17 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       ++cycles;
       // w = A z = -(0 - A z)
       resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
-      CK(cudaMemsetAsync(S->kdots, 0, sizeof(double) * (m + 2), S->stream));
-      for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
-        k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);
-        k_axpy_dev<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, S->kdots + i, N);
+      {
+        // modified Gram-Schmidt: per basis vector a dot (2 reads) and an update (2 reads, 1 write)
+        ProfScope ps(S, P_KRYLOV, (double)(j + 1) * 40.0 * N + 32.0 * N, 2 * (j + 1) + 2);
+        CK(cudaMemsetAsync(S->kdots, 0, sizeof(double) * (m + 2), S->stream));
+        for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
+          k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);
+          k_axpy_dev<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, S->kdots + i, N);
+        }
+        k_dot<<<grid, block, 0, S->stream>>>(S->kw, S->kw, N, S->kdots + j + 1);
+        k_scale_norm<<<grid, block, 0, S->stream>>>(V + (long long)(j + 1) * N, S->kw, S->kdots + j + 1, -1.0, N);
       }
-      k_dot<<<grid, block, 0, S->stream>>>(S->kw, S->kw, N, S->kdots + j + 1);
-      k_scale_norm<<<grid, block, 0, S->stream>>>(V + (long long)(j + 1) * N, S->kw, S->kdots + j + 1, -1.0, N);
       CK(cudaMemcpyAsync(S->khdots, S->kdots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, S->stream));
       CK(cudaStreamSynchronize(S->stream));
       // column j of H (the dots were taken with -w = -A z)
@@ -1225,7 +1384,10 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       y[i] = s / H[(size_t)i * m + i];
     }
     CK(cudaMemcpyAsync(S->kdots + m + 2, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, S->stream));
-    k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
+    {
+      ProfScope ps(S, P_KRYLOV, (8.0 * k + 8.0) * N);
+      k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
+    }
     cc_status pst = apply_prec(S, S->kw);
     if (pst) return pst;
     ++cycles;
@@ -1251,6 +1413,10 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter V-cycles";
   if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (take_timeout(S)) {
+    S->err = "a grid barrier of the LU sweeps waited too long";
+    return CC_ERR_TIMEOUT;
+  }
   return result;
 }
 
@@ -1308,6 +1474,7 @@ void cc_default_params(cc_params* p) {
   p->krylov = 0;
   p->krylov_restart = 30;
   p->precision = 0;
+  p->lu_schedule = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1356,7 +1523,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   else
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
-      S->prm.precision < 0 || S->prm.precision > 2) {
+      S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }
@@ -1471,6 +1638,10 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   }
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) S->nsm = prop.multiProcessorCount;
+  {
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) == cudaSuccess) S->coop = coop != 0;
+  }
   if (cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete S;
     return CC_ERR_CUDA;
@@ -1523,6 +1694,11 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dalloc(S, &S->f, D0.N));
     TRY(dalloc(S, &S->gbox, (size_t)6 * L0.n * L0.n));
     TRY(dalloc(S, &S->norm, 1));
+    TRY(dalloc(S, &S->err_flag, 1));
+    if (cudaMemset(S->err_flag, 0, sizeof(unsigned int)) != cudaSuccess) {
+      st = CC_ERR_CUDA;
+      goto failed;
+    }
     if (cudaMallocHost((void**)&S->hnorm, sizeof(double)) != cudaSuccess) {
       st = CC_ERR_OOM;
       goto failed;
@@ -1755,6 +1931,7 @@ cc_status cc_lu_correction(cc_solver* S, int level, double* phi, const double* r
   if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
   lu_solve<double>(S, S->lev[level].lu, rhs, phi);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
   return CC_OK;
 }
 
@@ -1787,6 +1964,7 @@ cc_status cc_bottom_solve(cc_solver* S, const double* rhs, double* phi) {
   CK(cudaMemsetAsync(phi, 0, L.N * sizeof(double), S->stream));
   lu_solve<double>(S, L.lu, rhs, phi);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
   return CC_OK;
 }
 
@@ -1795,6 +1973,7 @@ cc_status cc_vcycle(cc_solver* S, const double* rhs, double* e) {
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   precond(S, rhs, e);
   CK(cudaGetLastError());
+  if (take_timeout(S)) return fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
   return CC_OK;
 }
 
@@ -1871,6 +2050,7 @@ cc_status cc_lu_correction_static(cc_solver* S, int level, double* phi, const do
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = fail(S, CC_ERR_CUDA, std::string("cc_lu_correction_static: ") + cudaGetErrorString(e));
+    else if (take_timeout(S)) st = fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
   }
   if (prev != S->device) cudaSetDevice(prev);
   return st;

@@ -238,3 +238,23 @@ def test_mixed_precision_solve(pair, krylov, precision):
     ref, hist, it = H.multigrid(r_or, eps=1e-10)
     assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
     K.close()
+
+
+def test_lu_schedules_agree(pair):
+    """The one-launch cooperative sweep schedule gives the same LU-correction as
+    one launch per tree height (to FP64 rounding of the atomic adds)."""
+    from paper_2410_05865_gb300 import ccmg
+    S, H, _, _, prob = pair
+    lv = H.levels[0]
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, lu_schedule=1)
+    phi = rand_unknowns(lv, 11)
+    s = rand_unknowns(lv, 12) * 1e3
+    a = dev(to_grid(lv, phi))
+    b = dev(to_grid(lv, phi))
+    S.lu_correction(0, a, dev(to_grid(lv, s)))
+    K.lu_correction(0, b, dev(to_grid(lv, s)))
+    S.sync()
+    K.sync()
+    ga, gb_ = a.cpu().numpy(), b.cpu().numpy()
+    assert np.abs(ga - gb_).max() < 1e-11 * np.abs(ga).max()
+    K.close()

@@ -318,7 +318,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = S.profile_entries()
     S.profile(False)
-    launches = sum(v[0] for v in prof.values())
+    # launches of one profiled solve, scaled to the timed steps by their V-cycle counts
+    launches = sum(v[0] for v in prof.values()) * sum(iters) / max(1, st_p.iters)
     top = max(prof.items(), key=lambda kv: kv[1][1])
     name, (cnt, kms, kbytes) = top
     hbm, src = peaks()

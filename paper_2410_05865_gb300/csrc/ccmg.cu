@@ -138,96 +138,26 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
 }
 
 // Grid kernels run on a 3-D launch: threads along k, blockIdx.y = j, blockIdx.z = i.
-// SMO-1 with 2.5-D blocking: a BY x BX tile of (j, k) columns marches along i over
-// IC planes.  Plane i (with a 2-cell halo in j and k) is staged in shared memory,
-// the i -+ 1, 2 neighbours of each column ride in a register queue, so each value
-// is read from HBM/L2 about once instead of through 13 scattered loads.  The
-// loads of plane i+1 (tile part, s and typ) are issued before plane i is
-// computed, so one memory latency per plane overlaps the arithmetic.  Cells
-// whose row is not the interior row (near the box) take apply_regular.
-template <class T, int BX, int BY, int IC>
-__global__ void __launch_bounds__(BX * BY) k_jacobi_tiled(const T* __restrict__ phi_in, const T* __restrict__ s,
-                                                           T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
-                                                           StencilP P) {
-  constexpr int TW = BX + 4, NT = (BY + 4) * TW, PER = (NT + BX * BY - 1) / (BX * BY);
-  __shared__ T tile[BY + 4][TW];
+// SMO-1: one thread per cell on a 32 x 8 (k, j) tile of one plane, so the j and
+// k neighbours of a warp's loads come from the same or adjacent cache lines and
+// the i neighbours from L2; measured faster on GB300 than staging planes in
+// shared memory (the cached working set of a plane tile is small).
+template <class T>
+__global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
+                                               T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
+                                               StencilP P) {
   const int n = P.n;
-  const long long nn = (long long)n * n;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int k0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
-  const int k = k0 + tx, j = j0 + ty;
-  const int i0 = blockIdx.z * IC;
-  const int i1 = min(i0 + IC, n);
-  const bool inb = k < n && j < n;
-  const long long col = (long long)j * n + k;
-  // this thread's tile slots e = tid + p BX BY: in-plane offset, or -1 outside the grid / tile
-  long long goff[PER];
-#pragma unroll
-  for (int p = 0; p < PER; ++p) {
-    const int e = tid + p * BX * BY;
-    const int ly = e / TW, lx = e - ly * TW;
-    const int jj = j0 + ly - 2, kk = k0 + lx - 2;
-    goff[p] = (e < NT && jj >= 0 && jj < n && kk >= 0 && kk < n) ? (long long)jj * n + kk : -1;
+  const int k = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, i = blockIdx.z;
+  if (k >= n || j >= n) return;
+  const long long idx = ((long long)i * n + j) * n + k;
+  const T v = phi_in[idx];
+  T res = v;
+  if (typ[idx] == 1) {
+    const T lphi = apply_regular<T>(phi_in, i, j, k, P);
+    res = fma_t(st_winv<T>(P, pos_class(i, n), pos_class(j, n), pos_class(k, n)), s[idx] - lphi, v);
   }
-  T pre[PER];
-#pragma unroll
-  for (int p = 0; p < PER; ++p) pre[p] = goff[p] >= 0 ? phi_in[(long long)i0 * nn + goff[p]] : T(0);
-  T s_nx = T(0);
-  uint8_t t_nx = 0;
-  if (inb) {
-    s_nx = s[(long long)i0 * nn + col];
-    t_nx = typ[(long long)i0 * nn + col];
-  }
-  // q[t] = phi(i - 2 + t) of this column; q[2] is also in the tile
-  T q[5];
-#pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    const int ii = i0 - 2 + t;
-    q[t] = (inb && ii >= 0 && ii < n) ? phi_in[(long long)ii * nn + col] : T(0);
-  }
-  const int cj = pos_class(j, n), ck = pos_class(k, n);
-  for (int i = i0; i < i1; ++i) {
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int e = tid + p * BX * BY;
-      if (e < NT) (&tile[0][0])[e] = pre[p];
-    }
-    __syncthreads();
-    const T s_cur = s_nx;
-    const uint8_t t_cur = t_nx;
-    if (i + 1 < i1) {
-#pragma unroll
-      for (int p = 0; p < PER; ++p) pre[p] = goff[p] >= 0 ? phi_in[(long long)(i + 1) * nn + goff[p]] : T(0);
-      if (inb) {
-        s_nx = s[(long long)(i + 1) * nn + col];
-        t_nx = typ[(long long)(i + 1) * nn + col];
-      }
-    }
-    if (inb) {
-      const long long idx = (long long)i * nn + col;
-      const T v = q[2];
-      T res = v;
-      if (t_cur == 1) {
-        const int ci = pos_class(i, n);
-        T lphi;
-        if (ci == 2 && cj == 2 && ck == 2) {
-          const int y = ty + 2, x = tx + 2;
-          lphi = interior13<T>(v, q[3], q[1], tile[y + 1][x], tile[y - 1][x], tile[y][x + 1], tile[y][x - 1], q[4],
-                               q[0], tile[y + 2][x], tile[y - 2][x], tile[y][x + 2], tile[y][x - 2], st_inv<T>(P));
-        } else {
-          lphi = apply_regular<T>(phi_in, i, j, k, P);
-        }
-        res = fma_t(st_winv<T>(P, ci, cj, ck), s_cur - lphi, v);
-      }
-      phi_out[idx] = res;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) q[t] = q[t + 1];
-    q[4] = (inb && i + 3 < n) ? phi_in[(long long)(i + 3) * nn + col] : T(0);
-  }
+  phi_out[idx] = res;
 }
-constexpr int kJBX = 32, kJBY = 8, kJIC = 16;
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
@@ -1008,8 +938,8 @@ void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
   const int block = 256;
   ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
   (void)block;
-  const dim3 grid((L.n + kJBX - 1) / kJBX, (L.n + kJBY - 1) / kJBY, (L.n + kJIC - 1) / kJIC);
-  k_jacobi_tiled<T, kJBX, kJBY, kJIC><<<grid, dim3(kJBX, kJBY), 0, S->stream>>>(in, s, out, L.typ, L.P);
+  const dim3 grid((L.n + 31) / 32, (L.n + 7) / 8, L.n);
+  k_jacobi<T><<<grid, dim3(32, 8), 0, S->stream>>>(in, s, out, L.typ, L.P);
 }
 
 void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {

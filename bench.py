@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape-bc", default="dirichlet", choices=["dirichlet", "neumann"],
                     help="boundary kind on the ellipsoids (the box is Dirichlet)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: the 256^3 solve; batch: --batch independent solves of mixed sizes")
+    ap.add_argument("--batch", type=int, default=16, help="solves in the batch workload")
     return ap.parse_args()
 
 
@@ -387,10 +390,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Independent solves of uneven sizes (64^3-192^3, 1-4 spheres or ellipsoids,
+    Gaussian-bump right-hand sides), timed one after another with cc_solve and
+    together with cc_solve_batch.  Each step solves every problem to 1e-10."""
+    import torch
+
+    import workloads as W
+    from paper_2410_05865_gb300 import ccmg
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    probs = [W.batch_problem(args.seed * 1000 + i) for i in range(args.batch)]
+    if args.shape_bc == "dirichlet":
+        for p in probs:
+            p.shape_bc = W.DIRICHLET
+    kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=16, krylov_restart=args.restart,
+              max_iter=2000)
+    t0 = time.time()
+    solvers, inputs, phis = [], [], []
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    for p in probs:
+        S = ccmg.Solver(p.n, p.shapes, p.shape_bc, p.box_bc, device=local, **kw)
+        f = ccmg.cell_averages_terms(S, W.rhs_terms(p))
+        gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact, p.box_bc)
+        gp = ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, p.shape_bc)
+        solvers.append(S)
+        inputs.append((dev(f), dev(gb), dev(gp)))
+        phis.append(torch.zeros(p.n ** 3, dtype=torch.float64, device="cuda"))
+    setup_s = time.time() - t0
+    unknowns = sum(S.info.n_unknowns[0] for S in solvers)
+
+    def seq():
+        its = 0
+        for S, (f, gb, gp), phi in zip(solvers, inputs, phis):
+            phi.zero_()
+            st, rc = S.solve(f, gb, gp, phi)
+            if rc != 0:
+                raise RuntimeError(f"solve failed: status {rc}")
+            its += st.iters
+        return its
+
+    def bat():
+        for phi in phis:
+            phi.zero_()
+        rc, stats, status = ccmg.solve_batch(solvers, [x[0] for x in inputs], [x[1] for x in inputs],
+                                             [x[2] for x in inputs], phis)
+        if rc != 0:
+            raise RuntimeError(f"batch failed: {status}")
+        return sum(st.iters for st in stats)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        t = time.perf_counter()
+        its = 0
+        for _ in range(args.steps):
+            its = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3 / args.steps, its
+
+    ms_seq, its_seq = timed(seq)
+    ms_bat, its_bat = timed(bat)
+    ms_bat = max_over_ranks(ms_bat, world)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "batched independent solves to 1e-10, total MDOF/s", "value": unknowns * world / ms_bat / 1e3,
+            "unit": "MDOF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bat,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ["f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic", "impl": "batch",
+            "config": {"workload": f"{args.batch} solves, sizes from {{64,96,128,160,192}}^3, 1-4 spheres or "
+                                   f"ellipsoids, Gaussian-bump RHS, {args.shape_bc} on the shapes",
+                       "sizes": [p.n for p in probs], "unknowns": unknowns, "setup_s": round(setup_s, 1),
+                       "v_cycles_total": its_bat,
+                       "one_after_another": {"ms": ms_seq, "mdof_s": unknowns / ms_seq / 1e3, "v_cycles": its_seq},
+                       "host_timer": "wall clock around the whole step, synchronised"}}))
+    for S in solvers:
+        S.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -60,7 +60,7 @@ typedef struct {
 } cc_shape;
 
 typedef struct {
-  int n;                  /* cells per axis on the finest level (>= 16, even for coarsening) */
+  int n;                  /* cells per axis on the finest level (16..1024, even for coarsening) */
   int nshapes;
   const cc_shape* shapes; /* removed from the box [0,1]^3 */
   int shape_bc;           /* CC_DIRICHLET or CC_NEUMANN on every shape */
@@ -169,6 +169,17 @@ cc_status cc_rhs(cc_solver* s, const double* f, const double* g_box, const doubl
  * Returns CC_ERR_NOT_CONVERGED (phi = last iterate) or CC_ERR_DIVERGED. */
 cc_status cc_solve(cc_solver* s, const double* f, const double* g_box, const double* g_patch, double* phi,
                    int where, cc_stats* stats);
+/* Many independent solves at once (the batched form of cc_solve; no paper
+ * counterpart).  Each solver keeps its own geometry, grid size, parameters and
+ * stream; the call drives every solve from its own host thread, so the small
+ * solves' kernels and graphs overlap on the GPU.  Arrays have nb entries and
+ * follow cc_solve (f, g_box, g_patch and phi of solve i in its own layout);
+ * stats and status (either may be NULL) receive each solve's outcome.  Returns
+ * CC_OK if every solve converged, else the first failing status.  Two solvers
+ * in one batch must not share a stream (cc_set_stream). */
+cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, const double* const* g_box,
+                         const double* const* g_patch, double* const* phi, int where, cc_stats* stats,
+                         cc_status* status);
 /* The same iteration for an already assembled r (grid array). */
 cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_stats* stats);
 

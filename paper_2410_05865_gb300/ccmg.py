@@ -82,6 +82,8 @@ SIGNATURES = {
     "cc_solve_r": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(cc_stats)]),
     "cc_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "cc_jacobi": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "cc_solve_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                 C.POINTER(_P), C.c_int, _P, C.POINTER(C.c_int)]),
     "cc_lu_correction": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_lu_correction_static": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_restrict_residual": (C.c_int, [_P, C.c_int, _P, _P, _P]),
@@ -312,6 +314,22 @@ class Solver:
             out[name.decode()] = (n.value, ms.value, by.value)
             k += 1
         return out
+
+
+def solve_batch(solvers, fs, g_boxes, g_patches, phis, where=None):
+    """cc_solve_batch: solve i is solvers[i] with fs[i], g_boxes[i], g_patches[i]
+    and phis[i] (overwritten), all on the device (CUDA tensors) or all on the host.
+    Returns (overall status, [cc_stats], [status])."""
+    nb = len(solvers)
+    if where is None:
+        where = CC_HOST if nb and (isinstance(phis[0], np.ndarray) or not phis[0].is_cuda) else CC_DEVICE
+    arr = lambda xs: (_P * nb)(*[_ptr(x) for x in xs])
+    hs = (_P * nb)(*[S._h for S in solvers])
+    stats = (cc_stats * nb)()
+    status = (C.c_int * nb)()
+    rc = lib().cc_solve_batch(hs, nb, arr(fs), arr(g_boxes), arr(g_patches), arr(phis), where,
+                              C.cast(stats, _P), status)
+    return rc, list(stats), list(status)
 
 
 # ------------------------------------------------------- data preparation

@@ -17,7 +17,9 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -105,9 +107,10 @@ __device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1,
 // (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
 template <class T>
 __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int j, int k, const StencilP& P) {
+  // 32-bit indices: cc_setup limits n to 1024, so n^3 < 2^31
   const int n = P.n;
-  const long long nn = (long long)n * n;
-  const long long idx = (long long)i * nn + (long long)j * n + k;
+  const int nn = n * n;
+  const int idx = i * nn + j * n + k;
   const int ci = pos_class(i, n), cj = pos_class(j, n), ck = pos_class(k, n);
   if (ci == 2 && cj == 2 && ck == 2) {
     return interior13<T>(phi[idx], phi[idx + nn], phi[idx - nn], phi[idx + n], phi[idx - n], phi[idx + 1],
@@ -116,7 +119,7 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
   }
   // near the box: the ghost-eliminated 1-D rows, over each row's window of nonzero offsets
   const int cls[3] = {ci, cj, ck};
-  const long long stride[3] = {nn, (long long)n, 1};
+  const int stride[3] = {nn, n, 1};
   T acc = 0;
   if constexpr (sizeof(T) == 4) {  // differences from the centre, plus the rows' sum times the centre
     const T c0 = phi[idx];
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, co
   const int n = P.n;
   const int k = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, i = blockIdx.z;
   if (k >= n || j >= n) return;
-  const long long idx = ((long long)i * n + j) * n + k;
+  const int idx = (i * n + j) * n + k;
   const T v = phi_in[idx];
   T res = v;
   if (typ[idx] == 1) {
@@ -165,7 +168,7 @@ __global__ void k_resid1(const double* __restrict__ phi, const double* __restric
   const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
   double r = 0.0;
   if (k < n) {
-    const long long idx = ((long long)i * n + j) * n + k;
+    const int idx = (i * n + j) * n + k;
     if (typ[idx] == 1) r = s[idx] - apply_regular<double>(phi, i, j, k, P);
     out[idx] = r;
   }
@@ -204,10 +207,10 @@ __global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int i = 2 * a + (t >> 2), j = 2 * b + ((t >> 1) & 1), k = 2 * c + (t & 1);
-    const long long idx = ((long long)i * n + j) * n + k;
+    const int idx = (i * n + j) * n + k;
     if (typ[idx] == 1) acc += s[idx] - apply_regular<T>(phi, i, j, k, P);
   }
-  coarse[((long long)a * nc + b) * nc + c] = T(0.125) * acc;
+  coarse[(a * nc + b) * nc + c] = T(0.125) * acc;
 }
 
 // phi1 cells += the parent's correction, taken only from parents that are phi1
@@ -218,9 +221,9 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
   const int nc = n / 2;
   const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
   if (k >= n) return;
-  const long long idx = ((long long)i * n + j) * n + k;
+  const int idx = (i * n + j) * n + k;
   if (typ[idx] != 1) return;
-  const long long I = ((long long)(i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
+  const int I = ((i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
   if (typ_c[I] == 1) phi[idx] += coarse[I];
 }
 
@@ -266,7 +269,7 @@ __global__ void k_axpy_f(double* __restrict__ phi, const float* __restrict__ e, 
 // by a warp shuffle, and no cross-lane reduction is needed (on this GPU the FP64
 // adds of a shuffle reduction would cost as much as the products).  Partial row
 // sums go to the outputs with atomic adds.
-constexpr int kSegCols = 64;
+constexpr int kSegCols = 32;
 
 struct Task {
   long long moff;  // entry (r0, c0) of the column-major block
@@ -431,7 +434,7 @@ __global__ void k_rhs_base(const double* __restrict__ f, const double* __restric
   const int n = P.n;
   const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
   if (k >= n) return;
-  const long long idx = ((long long)i * n + j) * n + k;
+  const int idx = (i * n + j) * n + k;
   const uint8_t t = typ[idx];
   double v = t ? f[idx] : 0.0;
   if (t == 1) {
@@ -1445,7 +1448,8 @@ void cc_destroy(cc_solver* S) {
 }
 
 cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solver** out) {
-  if (!g || !out || g->n < 8 || g->nshapes < 0 || (g->nshapes > 0 && !g->shapes)) return CC_ERR_INVALID_ARG;
+  if (!g || !out || g->n < 8 || g->n > 1024 || g->nshapes < 0 || (g->nshapes > 0 && !g->shapes))
+    return CC_ERR_INVALID_ARG;
   *out = nullptr;
   cc_solver* S = new cc_solver();
   if (p)
@@ -1819,6 +1823,37 @@ cc_status cc_solve(cc_solver* S, const double* f, const double* g_box, const dou
                      where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
   k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
   return run_solve(S, phi, where, stats);
+}
+
+cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, const double* const* g_box,
+                         const double* const* g_patch, double* const* phi, int where, cc_stats* stats,
+                         cc_status* status) {
+  if (nb < 0 || (nb > 0 && (!s || !f || !g_box || !g_patch || !phi))) return CC_ERR_INVALID_ARG;
+  for (int i = 0; i < nb; ++i)
+    if (!s[i] || !phi[i] || s[i]->host_only) return CC_ERR_INVALID_ARG;
+  std::vector<cc_status> st(nb, CC_OK);
+  std::atomic<int> next(0);
+  // one host thread per solve in flight: each drives its solver's stream and
+  // graphs, so the solves' kernels overlap on the GPU
+  auto worker = [&]() {
+    for (int i = next.fetch_add(1); i < nb; i = next.fetch_add(1)) {
+      if (cudaSetDevice(s[i]->device) != cudaSuccess) {
+        st[i] = CC_ERR_CUDA;
+        continue;
+      }
+      st[i] = cc_solve(s[i], f[i], g_box[i], g_patch[i], phi[i], where, stats ? &stats[i] : nullptr);
+    }
+  };
+  const int nt = std::min(nb, 64);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  cc_status result = CC_OK;
+  for (int i = 0; i < nb; ++i) {
+    if (status) status[i] = st[i];
+    if (result == CC_OK && st[i] != CC_OK) result = st[i];
+  }
+  return result;
 }
 
 cc_status cc_solve_r(cc_solver* S, const double* r, double* phi, int where, cc_stats* stats) {

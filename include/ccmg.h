@@ -90,6 +90,9 @@ typedef struct {
                         0 one launch per tree height and sweep; 1 one cooperative
                         launch per solve with bounded grid barriers between heights
                         (falls back to 0 where cooperative launch is unavailable) (0) */
+  int krylov_cgs;    /* GMRES orthogonalisation: 0 modified Gram-Schmidt (a dot and an
+                        update per basis vector); 1 classical Gram-Schmidt in two
+                        fused passes over the basis (0) */
 } cc_params;
 
 typedef struct {

@@ -141,25 +141,55 @@ __device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int
 }
 
 // Grid kernels run on a 3-D launch: threads along k, blockIdx.y = j, blockIdx.z = i.
-// SMO-1: one thread per cell on a 32 x 8 (k, j) tile of one plane, so the j and
-// k neighbours of a warp's loads come from the same or adjacent cache lines and
-// the i neighbours from L2; measured faster on GB300 than staging planes in
-// shared memory (the cached working set of a plane tile is small).
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// SMO-1: one thread per pair of cells (k, k+1) on a 32 x 8 (k, j) tile of one
+// plane; interior pairs read their 13-point neighbourhoods as 2-element vector
+// loads (11 loads for two cells), pairs near the box take apply_regular.
 template <class T>
-__global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
+__global__ void __launch_bounds__(128) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
                                                T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
                                                StencilP P) {
+  using V2 = typename Vec2<T>::type;
   const int n = P.n;
-  const int k = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, i = blockIdx.z;
+  const int k = 2 * (blockIdx.x * 16 + threadIdx.x), j = blockIdx.y * 8 + threadIdx.y, i = blockIdx.z;
   if (k >= n || j >= n) return;
-  const int idx = (i * n + j) * n + k;
-  const T v = phi_in[idx];
-  T res = v;
-  if (typ[idx] == 1) {
-    const T lphi = apply_regular<T>(phi_in, i, j, k, P);
-    res = fma_t(st_winv<T>(P, pos_class(i, n), pos_class(j, n), pos_class(k, n)), s[idx] - lphi, v);
+  const int nn = n * n;
+  const int idx = (i * n + j) * n + k;  // even: n is even
+  const uchar2 t = *reinterpret_cast<const uchar2*>(typ + idx);
+  const V2 c = *reinterpret_cast<const V2*>(phi_in + idx);
+  V2 res = c;
+  if (t.x == 1 || t.y == 1) {
+    const V2 sv = *reinterpret_cast<const V2*>(s + idx);
+    const int ci = pos_class(i, n), cj = pos_class(j, n);
+    if (ci == 2 && cj == 2 && k >= 2 && k + 3 < n) {
+      auto ld = [&](int o) { return *reinterpret_cast<const V2*>(phi_in + idx + o); };
+      const V2 km = ld(-2), kp = ld(2);  // (k-2, k-1) and (k+2, k+3)
+      const V2 ip1 = ld(nn), im1 = ld(-nn), ip2 = ld(2 * nn), im2 = ld(-2 * nn);
+      const V2 jp1 = ld(n), jm1 = ld(-n), jp2 = ld(2 * n), jm2 = ld(-2 * n);
+      const T inv = st_inv<T>(P);
+      const T w = st_winv<T>(P, 2, 2, 2);
+      if (t.x == 1) {
+        const T l = interior13<T>(c.x, ip1.x, im1.x, jp1.x, jm1.x, c.y, km.y, ip2.x, im2.x, jp2.x, jm2.x, kp.x,
+                                  km.x, inv);
+        res.x = fma_t(w, sv.x - l, c.x);
+      }
+      if (t.y == 1) {
+        const T l = interior13<T>(c.y, ip1.y, im1.y, jp1.y, jm1.y, kp.x, c.x, ip2.y, im2.y, jp2.y, jm2.y, kp.y,
+                                  km.y, inv);
+        res.y = fma_t(w, sv.y - l, c.y);
+      }
+    } else {
+      if (t.x == 1)
+        res.x = fma_t(st_winv<T>(P, ci, cj, pos_class(k, n)), sv.x - apply_regular<T>(phi_in, i, j, k, P), c.x);
+      if (t.y == 1)
+        res.y = fma_t(st_winv<T>(P, ci, cj, pos_class(k + 1, n)), sv.y - apply_regular<T>(phi_in, i, j, k + 1, P),
+                      c.y);
+    }
   }
-  phi_out[idx] = res;
+  *reinterpret_cast<V2*>(phi_out + idx) = res;
 }
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
@@ -426,6 +456,53 @@ __global__ void k_combine(double* __restrict__ u, const double* __restrict__ V, 
     for (int j = 0; j < k; ++j) a += y[j] * V[(long long)j * N + i];
     u[i] = a;
   }
+}
+
+// Classical Gram-Schmidt in two passes over the basis (instead of a dot and an
+// update per basis vector): dots[i] += <w, V_i> for i < k, eight vectors per pass
+// over w (k_mdot), then w -= sum_i h_i V_i with ||w||^2 of the result (k_mupdate).
+constexpr int kMdotVec = 8;
+__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ w, const double* __restrict__ V, int k,
+                                             long long N, double* __restrict__ dots) {
+  for (int i0 = 0; i0 < k; i0 += kMdotVec) {
+    const int nv = min(kMdotVec, k - i0);
+    double acc[kMdotVec];
+#pragma unroll
+    for (int q = 0; q < kMdotVec; ++q) acc[q] = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+      const double wp = w[p];
+#pragma unroll
+      for (int q = 0; q < kMdotVec; ++q)
+        if (q < nv) acc[q] = fma(wp, V[(long long)(i0 + q) * N + p], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kMdotVec; ++q) {
+      if (q >= nv) break;
+      double a = acc[q];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      if ((threadIdx.x & 31) == 0 && a != 0.0) atomicAdd(dots + i0 + q, a);
+    }
+  }
+}
+
+// w -= sum_{i<k} h_i V_i (h from the device), and nrm2 += ||w||^2 of the result
+__global__ void __launch_bounds__(256) k_mupdate(double* __restrict__ w, const double* __restrict__ V,
+                                                const double* __restrict__ h, int k, long long N,
+                                                double* __restrict__ nrm2) {
+  __shared__ double hs[64];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    double v = w[p];
+    for (int i = 0; i < k; ++i) v = fma(-hs[i], V[(long long)i * N + p], v);
+    w[p] = v;
+    acc = fma(v, v, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(nrm2, acc);
 }
 
 // r = f for unknowns (0 elsewhere), minus the ghost terms of phi1 rows next to the box.
@@ -942,7 +1019,7 @@ void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
   ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
   (void)block;
   const dim3 grid((L.n + 31) / 32, (L.n + 7) / 8, L.n);
-  k_jacobi<T><<<grid, dim3(32, 8), 0, S->stream>>>(in, s, out, L.typ, L.P);
+  k_jacobi<T><<<grid, dim3(16, 8), 0, S->stream>>>(in, s, out, L.typ, L.P);
 }
 
 void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {
@@ -1278,13 +1355,21 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
       {
         // modified Gram-Schmidt: per basis vector a dot (2 reads) and an update (2 reads, 1 write)
-        ProfScope ps(S, P_KRYLOV, (double)(j + 1) * 40.0 * N + 32.0 * N, 2 * (j + 1) + 2);
+        ProfScope ps(S, P_KRYLOV,
+                     S->prm.krylov_cgs ? (2.0 * (j + 1) + 5.0 + (j + 1 + 7) / 8) * 8.0 * N
+                                       : (double)(j + 1) * 40.0 * N + 32.0 * N,
+                     S->prm.krylov_cgs ? 3 : 2 * (j + 1) + 2);
         CK(cudaMemsetAsync(S->kdots, 0, sizeof(double) * (m + 2), S->stream));
-        for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
-          k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);
-          k_axpy_dev<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, S->kdots + i, N);
+        if (S->prm.krylov_cgs) {  // classical Gram-Schmidt on -w: two passes over the basis
+          k_mdot<<<grid, block, 0, S->stream>>>(S->kw, V, j + 1, N, S->kdots);
+          k_mupdate<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots, j + 1, N, S->kdots + j + 1);
+        } else {
+          for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
+            k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);
+            k_axpy_dev<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, S->kdots + i, N);
+          }
+          k_dot<<<grid, block, 0, S->stream>>>(S->kw, S->kw, N, S->kdots + j + 1);
         }
-        k_dot<<<grid, block, 0, S->stream>>>(S->kw, S->kw, N, S->kdots + j + 1);
         k_scale_norm<<<grid, block, 0, S->stream>>>(V + (long long)(j + 1) * N, S->kw, S->kdots + j + 1, -1.0, N);
       }
       CK(cudaMemcpyAsync(S->khdots, S->kdots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, S->stream));
@@ -1408,6 +1493,7 @@ void cc_default_params(cc_params* p) {
   p->krylov_restart = 30;
   p->precision = 0;
   p->lu_schedule = 0;
+  p->krylov_cgs = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1883,6 +1969,7 @@ cc_status cc_jacobi(cc_solver* S, int level, const double* phi_in, const double*
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   cc_status st = check_level(S, level);
   if (st) return st;
+  if (S->lev[level].n % 2) return fail(S, CC_ERR_INVALID_ARG, "SMO-1 needs an even number of cells per axis");
   jacobi<double>(S, S->lev[level], phi_in, rhs, phi_out);
   CK(cudaGetLastError());
   return CC_OK;

@@ -257,6 +257,8 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
   if (typ_c[I] == 1) phi[idx] += coarse[I];
 }
 
+constexpr int kBarGroups = 16;  // group counters of the one-launch sweeps' grid barrier (after one top counter)
+
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
 // The PLG rows are applied in FP64 whatever the grid type; b is stored in the
 // LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
@@ -264,7 +266,7 @@ template <class T, class TW>
 __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                          const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
                          const T* __restrict__ s, const T* __restrict__ phi, unsigned int* __restrict__ bar) {
-  if (bar && blockIdx.x == 0 && threadIdx.x == 0) *bar = 0u;  // barrier counter of the one-launch sweeps
+  if (bar && blockIdx.x == 0 && threadIdx.x <= kBarGroups) bar[threadIdx.x] = 0u;  // one-launch sweep counters
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     double v = (double)s[cell[p]];
     for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
@@ -356,24 +358,30 @@ __global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
   for (int t = warp; t < ntasks; t += nwarps) run_tile<FWD, TV>(tasks[t], lane, vals, structs, b, x);
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks resident).  Arrival
-// counts accumulate over the launch; phase p completes at p * gridDim.x.  The
-// wait is bounded: on exhaustion err[0] is raised and every block returns at
-// its next barrier, so the kernel always ends.
-constexpr long long kBarrierSpins = 1ll << 23;  // about a second of __nanosleep(64)
+// Grid-wide barrier of a cooperative launch (all blocks resident).  Arrivals
+// are counted in two levels (a block on its group's counter, the last block of
+// a group on the top counter) so no single address takes one atomic per
+// block; phase p completes when the top counter reaches p * groups.  The wait
+// is bounded: on exhaustion err[0] is raised and every block returns at its
+// next barrier, so the kernel always ends.
+constexpr long long kBarrierSpins = 1ll << 24;  // about a second of polling
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int target, unsigned int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int phase, unsigned int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(bar, 1u);
+    const unsigned int g = blockIdx.x % kBarGroups;
+    const unsigned int gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
+    const unsigned int ngroups = min(gridDim.x, (unsigned int)kBarGroups);
+    if (atomicAdd(bar + 1 + g, 1u) + 1u == phase * gsize) atomicAdd(bar, 1u);
+    const unsigned int target = phase * ngroups;
     long long spins = 0;
     while (*(volatile unsigned int*)bar < target && *(volatile unsigned int*)err == 0u) {
       if (++spins > kBarrierSpins) {
         atomicExch(err, 1u);
         break;
       }
-      __nanosleep(64);
+      __nanosleep(32);
     }
     __threadfence();
   }
@@ -396,12 +404,12 @@ __global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
   for (int h = 0; h <= height; ++h) {
     const long long e = toff_f[h + 1];
     for (long long t = toff_f[h] + warp; t < e; t += nwarps) run_tile<true, TV>(tasks[t], lane, vals, structs, b, x);
-    if (!grid_barrier(bar, ++phase * gridDim.x, err)) return;
+    if (!grid_barrier(bar, ++phase, err)) return;
   }
   for (int h = height; h >= 0; --h) {
     const long long e = toff_b[h + 1];
     for (long long t = toff_b[h] + warp; t < e; t += nwarps) run_tile<false, TV>(tasks[t], lane, vals, structs, b, x);
-    if (h > 0 && !grid_barrier(bar, ++phase * gridDim.x, err)) return;
+    if (h > 0 && !grid_barrier(bar, ++phase, err)) return;
   }
 }
 
@@ -907,7 +915,7 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
     if ((st = dupload(S, &D.dtoff[sw], D.toff[sw]))) return st;
     for (double v : D.tbytes[sw]) D.sweep_bytes += v;
   }
-  if ((st = dalloc(S, &D.bar, 1))) return st;
+  if ((st = dalloc(S, &D.bar, 1 + kBarGroups))) return st;
   // one cooperative launch per solve when the device allows it: every block resident
   D.coop_grid = 0;
   if (S->coop && S->prm.lu_schedule == 1) {

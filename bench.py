@@ -314,7 +314,8 @@ def run_ours(args):
     h2d = int(fh.numel() * 8 + gbh.numel() * 8 + gph.numel() * 8 + phih.numel() * 8)
     d2h = int(phih.numel() * 8)
 
-    # per-kernel profile of one solve (events around every launch, graphs off)
+    # per-kernel profile of one solve: CUDA events around every launch, recorded
+    # inside the captured graphs (the same launch sequence as the timed solves)
     S.profile(True)
     with torch.cuda.stream(stream):
         st_p = step()
@@ -363,6 +364,8 @@ def run_ours(args):
                        "n": n, "unknowns": N, "levels": [info.n[m] for m in range(info.n_levels)],
                        "phi2_per_level": [info.n_phi2[m] for m in range(info.n_levels)],
                        "lu_entries_per_level": [info.lu_entries[m] for m in range(info.n_levels)],
+                       "smo1_tiles_tuned": [[2 * info.jacobi_block[m][0], info.jacobi_block[m][1]]
+                                            for m in range(info.n_levels - 1)],
                        "v_cycles": iters[-1], "omega": 0.5, "nu1": 3, "nu2": 3,
                        "precision": ["fp64",
                                      "fp32 grid work; fp64 LU-corrections, bottom solve, outer residual",

@@ -117,6 +117,8 @@ typedef struct {
   long long patch_nodes;      /* surface quadrature nodes of the patches */
   double ms_setup_host;
   double ms_setup_device;
+  int jacobi_block[16][2];    /* SMO-1 tile chosen by the set-up autotuner per level:
+                                 threads along k (two cells each) x rows along j */
 } cc_info;
 
 /* Fills the defaults given above. */

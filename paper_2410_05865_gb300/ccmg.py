@@ -58,7 +58,8 @@ class cc_info(C.Structure):
                 ("n_phi2", C.c_int * 16), ("lu_height", C.c_int * 16), ("lu_entries", C.c_longlong * 16),
                 ("phi2_nnz", C.c_longlong * 16), ("n_cut", C.c_int), ("n_patches", C.c_int),
                 ("cut_nodes", C.c_longlong), ("patch_nodes", C.c_longlong),
-                ("ms_setup_host", C.c_double), ("ms_setup_device", C.c_double)]
+                ("ms_setup_host", C.c_double), ("ms_setup_device", C.c_double),
+                ("jacobi_block", (C.c_int * 2) * 16)]
 
 
 # Every symbol include/ccmg.h declares, with its ctypes signature.

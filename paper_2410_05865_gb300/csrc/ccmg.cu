@@ -145,16 +145,18 @@ template <class T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// SMO-1: one thread per pair of cells (k, k+1) on a 32 x 8 (k, j) tile of one
-// plane; interior pairs read their 13-point neighbourhoods as 2-element vector
-// loads (11 loads for two cells), pairs near the box take apply_regular.
+// SMO-1: one thread per pair of cells (k, k+1) on a (2 blockDim.x) x blockDim.y
+// (k, j) tile of one plane (the tile shape is tuned per level at set-up);
+// interior pairs read their 13-point neighbourhoods as 2-element vector loads
+// (11 loads for two cells), pairs near the box take apply_regular.
 template <class T>
-__global__ void __launch_bounds__(128) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
+__global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
                                                T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
                                                StencilP P) {
   using V2 = typename Vec2<T>::type;
   const int n = P.n;
-  const int k = 2 * (blockIdx.x * 16 + threadIdx.x), j = blockIdx.y * 8 + threadIdx.y, i = blockIdx.z;
+  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = blockIdx.z;
   if (k >= n || j >= n) return;
   const int nn = n * n;
   const int idx = (i * n + j) * n + k;  // even: n is even
@@ -587,6 +589,7 @@ struct DevLU {
   int coop_grid = 0;               // blocks of the cooperative one-launch sweep (0: per-height launches)
   mutable bool coop_failed = false;  // the cooperative launch was refused: per-height launches from then on
   double sweep_bytes = 0;          // algorithmic bytes of one whole solve's sweeps
+  int nsweep_launches = 0;         // launches of the per-height schedule (non-empty heights, both sweeps)
   double *b = nullptr, *x = nullptr;  // work vectors of the sweeps
   float *b32 = nullptr, *x32 = nullptr;
   int* cell = nullptr;  // ND position -> grid index
@@ -608,6 +611,7 @@ struct DevLevel {
   DevLU lu;
   double *s = nullptr, *e = nullptr, *tmp = nullptr;
   float *s32 = nullptr, *e32 = nullptr, *tmp32 = nullptr;  // mixed precision V-cycle
+  dim3 jblock = dim3(16, 8);  // SMO-1 tile (pairs along k x rows along j), tuned at set-up
   template <class T> T* bs();
   template <class T> T* be();
   template <class T> T* btmp();
@@ -626,8 +630,6 @@ enum Prof {
   P_RESTRICT,
   P_PROLONG,
   P_LURHS,
-  P_FWD,
-  P_BWD,
   P_SCATTER,
   P_AXPY,
   P_NORM,
@@ -636,9 +638,8 @@ enum Prof {
   P_SWEEP,
   P_COUNT
 };
-const char* kProfNames[P_COUNT] = {"jacobi", "resid_phi1", "resid_phi2", "restrict", "prolong",
-                                   "lu_rhs", "lu_fwd",     "lu_bwd",     "lu_scatter", "axpy",
-                                   "norm",   "rhs",        "krylov",  "lu_sweeps"};
+const char* kProfNames[P_COUNT] = {"jacobi",     "resid_phi1", "resid_phi2", "restrict", "prolong", "lu_rhs",
+                                   "lu_scatter", "axpy",       "norm",       "rhs",      "krylov",  "lu_sweeps"};
 
 }  // namespace
 
@@ -685,6 +686,19 @@ struct cc_solver {
   double prof_ms[P_COUNT];
   double prof_bytes[P_COUNT];
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  // profiling inside captured graphs: event pairs recorded by every replay
+  struct GraphProf {
+    struct Scope {
+      int cls;
+      cudaEvent_t a, b;
+      int launches;
+      double bytes;
+    };
+    std::vector<Scope> scopes;
+    bool replayed = false;
+  };
+  GraphProf gprof_cycle, gprof_prec;
+  GraphProf* gprof_cur = nullptr;  // the list a capture in progress fills
   std::vector<void*> allocs;
   // host copies kept for diagnostics: per level the factored matrix (CSR) and factors
   std::vector<SuperLU> host_lu;
@@ -739,22 +753,59 @@ struct ProfScope {
   double bytes;
   int launches;  // kernel launches inside the scope
   cudaEvent_t a = nullptr, b = nullptr;
+  // inside a stream capture the records must be external, i.e. event-record
+  // nodes of the graph that every replay executes
+  void record(cudaEvent_t e) {
+    if (S->gprof_cur)
+      cudaEventRecordWithFlags(e, S->stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, S->stream);
+  }
   ProfScope(cc_solver* s, int c, double by, int nl = 1) : S(s), cls(c), bytes(by), launches(nl) {
     if (S->prof) {
       cudaEventCreate(&a);
       cudaEventCreate(&b);
-      cudaEventRecord(a, S->stream);
+      record(a);
     }
   }
-  ~ProfScope() {
+  bool open = true;
+  void close() {
+    if (!open) return;
+    open = false;
     if (S->prof) {
-      cudaEventRecord(b, S->stream);
-      S->pending.push_back({cls, {a, b}});
-      S->prof_launch[cls] += launches;
-      S->prof_bytes[cls] += bytes;
+      record(b);
+      if (S->gprof_cur) {  // inside a capture: the replays record the pair and are counted at flush
+        S->gprof_cur->scopes.push_back({cls, a, b, launches, bytes});
+      } else {
+        S->pending.push_back({cls, {a, b}});
+        S->prof_launch[cls] += launches;
+        S->prof_bytes[cls] += bytes;
+      }
     }
   }
+  ~ProfScope() { close(); }
 };
+
+// After a replay of a captured graph (stream synchronised): adds its scopes' times.
+void prof_flush_graph(cc_solver* S, cc_solver::GraphProf& g) {
+  if (!g.replayed) return;
+  for (auto& sc : g.scopes) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, sc.a, sc.b) == cudaSuccess) S->prof_ms[sc.cls] += ms;
+    S->prof_launch[sc.cls] += sc.launches;
+    S->prof_bytes[sc.cls] += sc.bytes;
+  }
+  g.replayed = false;
+}
+
+void prof_drop_graph(cc_solver::GraphProf& g) {
+  for (auto& sc : g.scopes) {
+    cudaEventDestroy(sc.a);
+    cudaEventDestroy(sc.b);
+  }
+  g.scopes.clear();
+  g.replayed = false;
+}
 
 void prof_flush(cc_solver* S) {
   if (S->pending.empty()) return;
@@ -914,6 +965,7 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   for (int sw = 0; sw < 2; ++sw) {
     if ((st = dupload(S, &D.dtoff[sw], D.toff[sw]))) return st;
     for (double v : D.tbytes[sw]) D.sweep_bytes += v;
+    for (int h = 0; h <= F.height; ++h) D.nsweep_launches += D.toff[sw][h + 1] > D.toff[sw][h] ? 1 : 0;
   }
   if ((st = dalloc(S, &D.bar, 1 + kBarGroups))) return st;
   // one cooperative launch per solve when the device allows it: every block resident
@@ -961,7 +1013,6 @@ void launch_sweep(cc_solver* S, const DevLU& D, const TV* vals, int sweep, int h
   if (nt <= 0) return;
   const int block = 256;
   const int grid = grid_for(S, (long long)nt * 32, block);
-  ProfScope ps(S, sweep == 0 ? P_FWD : P_BWD, D.tbytes[sweep][h]);
   if (sweep == 0)
     k_tasks<true, TV><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, vals, D.structs, b, x);
   else
@@ -983,8 +1034,10 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
     k_lu_rhs<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol, D.rval,
                                                                        s, phi, one ? D.bar : nullptr);
   }
+  // one profiling scope around both sweeps: inside a graph, per-launch event
+  // records would cost as much as the short launches they time
+  ProfScope sweep_scope(S, P_SWEEP, D.sweep_bytes, one ? 1 : D.nsweep_launches);
   if (one) {
-    ProfScope ps(S, P_SWEEP, D.sweep_bytes);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(D.coop_grid);
     cfg.blockDim = dim3(256);
@@ -1009,6 +1062,7 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
     for (int h = 0; h <= D.height; ++h) launch_sweep<TV>(S, D, vals, 0, h, b, x);
     for (int h = D.height; h >= 0; --h) launch_sweep<TV>(S, D, vals, 1, h, b, x);
   }
+  sweep_scope.close();
   ProfScope ps(S, P_SCATTER, (sizeof(TV) + 4.0 + sizeof(T)) * D.np);
   k_scatter<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
 }
@@ -1026,8 +1080,44 @@ void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
   const int block = 256;
   ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
   (void)block;
-  const dim3 grid((L.n + 31) / 32, (L.n + 7) / 8, L.n);
-  k_jacobi<T><<<grid, dim3(16, 8), 0, S->stream>>>(in, s, out, L.typ, L.P);
+  const dim3 tb = L.jblock;
+  const dim3 grid((L.n + 2 * tb.x - 1) / (2 * tb.x), (L.n + tb.y - 1) / tb.y, L.n);
+  k_jacobi<T><<<grid, tb, 0, S->stream>>>(in, s, out, L.typ, L.P);
+}
+
+// Set-up autotuner of the SMO-1 tile: times each candidate shape on the
+// level's own work arrays (contents irrelevant, results discarded) and keeps
+// the fastest for the V-cycle's precision.
+template <class T>
+cc_status tune_jacobi(cc_solver* S, DevLevel& L, T* a, T* b, T* c) {
+  static const int cand[][2] = {{16, 8}, {32, 4}, {8, 16}, {16, 16}, {32, 8}, {64, 2}, {64, 4}};
+  CK(cudaMemsetAsync(a, 0, L.N * sizeof(T), S->stream));
+  CK(cudaMemsetAsync(b, 0, L.N * sizeof(T), S->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  dim3 pick(16, 8);
+  for (const auto& cb : cand) {
+    const dim3 tb(cb[0], cb[1]);
+    if (2 * (int)tb.x > 2 * L.n) continue;
+    const dim3 grid((L.n + 2 * tb.x - 1) / (2 * tb.x), (L.n + tb.y - 1) / tb.y, L.n);
+    for (int w = 0; w < 2; ++w) k_jacobi<T><<<grid, tb, 0, S->stream>>>(a, b, c, L.typ, L.P);
+    CK(cudaEventRecord(e0, S->stream));
+    for (int r = 0; r < 5; ++r) k_jacobi<T><<<grid, tb, 0, S->stream>>>(a, b, c, L.typ, L.P);
+    CK(cudaEventRecord(e1, S->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = tb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.jblock = pick;
+  return CC_OK;
 }
 
 void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double* out, bool phi2, double* norm2) {
@@ -1167,6 +1257,8 @@ cc_status check_level(cc_solver* S, int level) {
 }
 
 void drop_graph(cc_solver* S) {
+  prof_drop_graph(S->gprof_cycle);
+  prof_drop_graph(S->gprof_prec);
   if (S->cycle_exec) {
     cudaGraphExecDestroy(S->cycle_exec);
     S->cycle_exec = nullptr;
@@ -1217,7 +1309,7 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   cc_status result = CC_ERR_NOT_CONVERGED;
   int it = 0;
   double rel = 0;
-  const bool use_graph = S->prm.use_graph && !S->prof;
+  const bool use_graph = S->prm.use_graph != 0;
   for (;; ++it) {
     if (S->prof) prof_flush(S);
     rel = rn > 0 ? std::sqrt(*S->hnorm) / rn : 0.0;
@@ -1234,17 +1326,21 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     if (use_graph) {
       if (!S->cycle_exec) {
         cudaGraph_t g;
+        S->gprof_cur = S->prof ? &S->gprof_cycle : nullptr;
         CK(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
         one_cycle(S);
+        S->gprof_cur = nullptr;
         CK(cudaStreamEndCapture(S->stream, &g));
         CK(cudaGraphInstantiate(&S->cycle_exec, g, 0));
         cudaGraphDestroy(g);
       }
       CK(cudaGraphLaunch(S->cycle_exec, S->stream));
+      S->gprof_cycle.replayed = true;
     } else {
       one_cycle(S);
     }
     CK(cudaStreamSynchronize(S->stream));
+    if (S->prof) prof_flush_graph(S, S->gprof_cycle);
   }
   {
     ProfScope ps(S, P_SCATTER, 0.0);
@@ -1283,20 +1379,23 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
 // otherwise be issued one by one from the host).
 cc_status apply_prec(cc_solver* S, const double* v) {
   DevLevel& L = S->lev[0];
-  if (!S->prm.use_graph || S->prof) {
+  if (!S->prm.use_graph) {
     precond(S, v, L.e);
     return CC_OK;
   }
   CK(cudaMemcpyAsync(S->kin, v, L.N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream));
   if (!S->prec_exec) {
     cudaGraph_t g;
+    S->gprof_cur = S->prof ? &S->gprof_prec : nullptr;
     CK(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
     precond(S, S->kin, L.e);
+    S->gprof_cur = nullptr;
     CK(cudaStreamEndCapture(S->stream, &g));
     CK(cudaGraphInstantiate(&S->prec_exec, g, 0));
     cudaGraphDestroy(g);
   }
   CK(cudaGraphLaunch(S->prec_exec, S->stream));
+  S->gprof_prec.replayed = true;
   return CC_OK;
 }
 
@@ -1335,6 +1434,10 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   while (true) {
     outer_residual(S);  // s0 = r - L phi, ||s0||^2 -> hnorm
     CK(cudaStreamSynchronize(S->stream));
+    if (S->prof) {
+      prof_flush_graph(S, S->gprof_prec);
+      prof_flush(S);
+    }
     const double beta = std::sqrt(*S->hnorm);
     rel = rn > 0 ? beta / rn : 0.0;
     if (stats && hist_n < 256) stats->resid_hist[hist_n++] = rel;
@@ -1382,6 +1485,7 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       }
       CK(cudaMemcpyAsync(S->khdots, S->kdots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, S->stream));
       CK(cudaStreamSynchronize(S->stream));
+      if (S->prof) prof_flush_graph(S, S->gprof_prec);
       // column j of H (the dots were taken with -w = -A z)
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = -S->khdots[i];
       double hnext = std::sqrt(std::max(0.0, S->khdots[j + 1]));
@@ -1767,6 +1871,17 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dupload(S, &S->a_cell, acell));
     TRY(dupload(S, &S->a_own, aown));
   }
+  // SMO-1 tile per smoothed level, for the V-cycle's precision
+  for (int m = 0; m < M; ++m) {
+    DevLevel& D = S->lev[m];
+    if (D.n % 2) continue;
+    if (S->prm.precision >= 1)
+      TRY(tune_jacobi<float>(S, D, D.e32, D.s32, D.tmp32));
+    else
+      TRY(tune_jacobi<double>(S, D, D.e, D.s, D.tmp));
+    S->info.jacobi_block[m][0] = (int)D.jblock.x;
+    S->info.jacobi_block[m][1] = (int)D.jblock.y;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     st = CC_ERR_CUDA;
     goto failed;
@@ -2041,9 +2156,10 @@ cc_status cc_profile(cc_solver* S, int enable) {
   if (!S) return CC_ERR_INVALID_ARG;
   if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
   prof_flush(S);
+  // graphs are re-captured with (or without) the profiling event nodes
+  if ((enable != 0) != S->prof) drop_graph(S);
   S->prof = enable != 0;
   if (S->prof) {
-    drop_graph(S);
     for (int k = 0; k < P_COUNT; ++k) {
       S->prof_launch[k] = 0;
       S->prof_ms[k] = 0;

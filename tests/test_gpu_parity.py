@@ -258,3 +258,12 @@ def test_lu_schedules_agree(pair):
     ga, gb_ = a.cpu().numpy(), b.cpu().numpy()
     assert np.abs(ga - gb_).max() < 1e-11 * np.abs(ga).max()
     K.close()
+
+
+def test_smo1_tiles_tuned(pair):
+    """The set-up autotuner picks one of its candidate SMO-1 tiles for every
+    smoothed level (the Jacobi parity above runs with that tile)."""
+    S, H, _, _, _ = pair
+    cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4)}
+    for m in range(len(H.levels) - 1):
+        assert tuple(S.info.jacobi_block[m]) in cands

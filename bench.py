@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--krylov", type=int, default=1, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
     ap.add_argument("--min-n", type=int, default=32, help="coarsening stops before n < min-n")
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--prolong", type=int, default=1,
+                    help="0 the paper's piecewise-constant prolongation; 1 trilinear cell-centred")
     ap.add_argument("--no-fp64-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape-bc", default="dirichlet", choices=["dirichlet", "neumann"],
@@ -252,7 +254,7 @@ def run_ours(args):
     prob = problem(W, n, args)
     t0 = time.time()
     solver_kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n,
-                     krylov_restart=args.restart, max_iter=2000)
+                     krylov_restart=args.restart, max_iter=2000, prolong=args.prolong)
     S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **solver_kw)
     setup_s = time.time() - t0
     stream = torch.cuda.Stream()
@@ -372,6 +374,8 @@ def run_ours(args):
                                      "fp32 grid work and LU-correction factors; fp64 PLG rows, bottom solve, "
                                      "outer residual"][args.precision],
                        "outer": ["Alg. Multigrid", f"GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
+                       "prolongation": ["piecewise constant (the paper's Prolong)",
+                                        "trilinear cell-centred over coarse phi1 cells"][args.prolong],
                        "plain_fp64_same_solver": fp64,
                        "setup_s": round(setup_s, 1), "parallelism": f"replicas x{world}",
                        "l2": "no flush: working set of several GB > 129 MB L2"},
@@ -405,7 +409,7 @@ def run_batch(args):
     world, rank, local = dist_init(args)
     torch.cuda.set_device(local)
     kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=16, krylov_restart=args.restart,
-              max_iter=2000)
+              max_iter=2000, prolong=args.prolong)
     t0 = time.time()
     probs, solvers, inputs, phis, skipped = [], [], [], [], []
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()

@@ -93,6 +93,9 @@ typedef struct {
   int krylov_cgs;    /* GMRES orthogonalisation: 0 modified Gram-Schmidt (a dot and an
                         update per basis vector); 1 classical Gram-Schmidt in two
                         fused passes over the basis (0) */
+  int prolong;       /* coarse-grid correction: 0 the paper's piecewise-constant
+                        prolongation (Prolong); 1 trilinear cell-centred weights from
+                        the 8 nearest coarse phi1 cells (0) */
 } cc_params;
 
 typedef struct {

@@ -259,6 +259,49 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
   if (typ_c[I] == 1) phi[idx] += coarse[I];
 }
 
+// Trilinear (cell-centred) prolongation, an option beside the paper's piecewise-
+// constant one: a fine phi1 cell takes the 3/4-1/4 tensor-product weights of
+// its 8 nearest coarse cell centres, using only coarse phi1 cells and
+// renormalising the weights over those (so constants are prolongated exactly).
+template <class T>
+__global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
+                              const uint8_t* __restrict__ typ_c, int n) {
+  const int nc = n / 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const int idx = (i * n + j) * n + k;
+  if (typ[idx] != 1) return;
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1, dk = (k & 1) ? 1 : -1;
+  T acc = T(0), wsum = T(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int ii = I + a * di;
+    if (ii < 0 || ii >= nc) continue;
+    const T wa = a ? T(0.25) : T(0.75);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int jj = J + b * dj;
+      if (jj < 0 || jj >= nc) continue;
+      const T wb = b ? T(0.25) : T(0.75);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int kk = K + c * dk;
+        if (kk < 0 || kk >= nc) continue;
+        const int q = (ii * nc + jj) * nc + kk;
+        if (typ_c[q] != 1) continue;
+        const T w = wa * wb * (c ? T(0.25) : T(0.75));
+        acc += w * coarse[q];
+        wsum += w;
+      }
+    }
+  }
+  if (wsum == T(1))
+    phi[idx] += acc;
+  else if (wsum > T(0))
+    phi[idx] += acc / wsum;
+}
+
 constexpr int kBarGroups = 16;  // group counters of the one-launch sweeps' grid barrier (after one top counter)
 
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
@@ -1147,7 +1190,11 @@ void prolong(cc_solver* S, int m, const T* coarse, T* phi) {
   const int block = 256;
   ProfScope ps(S, P_PROLONG, (2.0 * sizeof(T) + 1.0 + (sizeof(T) + 1.0) / 8.0) * L.N);
   (void)block;
-  k_prolong<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
+  if (S->prm.prolong == 1)
+    k_prolong_tri<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ,
+                                                                             L.n);
+  else
+    k_prolong<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
 }
 
 template <class T>
@@ -1606,6 +1653,7 @@ void cc_default_params(cc_params* p) {
   p->precision = 0;
   p->lu_schedule = 0;
   p->krylov_cgs = 0;
+  p->prolong = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1655,7 +1703,8 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   else
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
-      S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1) {
+      S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
+      S->prm.prolong < 0 || S->prm.prolong > 1) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }

@@ -1,0 +1,127 @@
+"""The bench workload at full size (three ellipsoids, 256^3, Dirichlet data,
+precision 2 with GMRES(30), trilinear prolongation, as bench.py runs it),
+checked on sampled outputs.
+
+The oracle cannot build the 256^3 hierarchy in test time, so the solution is
+checked against what holds at any size, computed here on the host without the
+CUDA path or the library's host setup:
+* the discrete equations: at sampled phi1 cells away from the box and the
+  shapes, the 13-point row of eq. regularLaplaceDiscretization applied to the
+  returned cell averages reproduces the right-hand side <f> to within the
+  final relative residual times ||r|| (a bound on every row of the residual);
+* the discretisation: at sampled full cells the returned averages match the
+  exact cell averages of the manufactured phi (closed-form 1-D averages of
+  sin and exp) to the fourth-order error level (1e-6 relative at h = 1/256).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N = 256
+
+
+def _avg_sin(a, h):
+    """Average of sin(2 pi x) over [a, a + h]."""
+    w = 2.0 * math.pi
+    return (np.cos(w * a) - np.cos(w * (a + h))) / (w * h)
+
+
+def _avg_exp(a, h):
+    return (np.exp(a + h) - np.exp(a)) / h
+
+
+def exact_average(i, j, k, h):
+    """Cell average of phi_exact over the full cell (i, j, k)."""
+    x, y, z = i * h, j * h, k * h
+    return (_avg_sin(x, h) * _avg_sin(y, h) * _avg_sin(z, h)
+            + 0.1 * _avg_exp(x, h) * _avg_exp(y, h) * _avg_exp(z, h))
+
+
+@pytest.fixture(scope="module")
+def solved():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_05865_gb300 import ccmg
+    prob = W.ellipsoids_problem(N, 0)
+    prob.shape_bc = W.DIRICHLET
+    S = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, precision=2, krylov=1,
+                    min_coarse_n=32, krylov_restart=30, max_iter=2000, prolong=1)
+    f = ccmg.cell_averages_terms(S, W.rhs_terms(prob))
+    gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact, prob.box_bc)
+    gp = ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, prob.shape_bc)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    st, rc = S.solve(dev(f), dev(gb), dev(gp), phi)
+    r = S.rhs(dev(f), dev(gb), dev(gp)).cpu().numpy()  # r = f - N g, the system's right-hand side
+    kind, typ, owner, vol = S.cell_map(0)
+    out = (st, rc, f, phi.cpu().numpy(), kind, typ, float(np.sqrt(np.sum(r[typ > 0] ** 2))))
+    S.close()
+    return out
+
+
+def _interior_phi1_sample(typ, count, seed):
+    """phi1 cells at least 3 cells from the box whose 13-point stencil is all phi1."""
+    rng = np.random.default_rng(seed)
+    t = typ.reshape(N, N, N)
+    picks = []
+    while len(picks) < count:
+        i, j, k = rng.integers(3, N - 3, 3)
+        if t[i, j, k] != 1:
+            continue
+        picks.append((i, j, k))
+    return np.array(picks)
+
+
+def test_fullsize_converges(solved):
+    st, rc, *_ = solved
+    assert rc == 0 and st.converged and st.rel_resid < 1e-10
+
+
+def test_fullsize_discrete_equations_hold(solved):
+    st, rc, f, phi, kind, typ, rnorm = solved
+    u = phi.reshape(N, N, N)
+    fg = f.reshape(N, N, N)
+    h = 1.0 / N
+    worst = 0.0
+    terms = 0.0
+    for i, j, k in _interior_phi1_sample(typ, 4000, 7):
+        lap = 0.0
+        for d in range(3):
+            e = [0, 0, 0]
+            e[d] = 1
+            m1 = u[i - e[0], j - e[1], k - e[2]]
+            p1 = u[i + e[0], j + e[1], k + e[2]]
+            m2 = u[i - 2 * e[0], j - 2 * e[1], k - 2 * e[2]]
+            p2 = u[i + 2 * e[0], j + 2 * e[1], k + 2 * e[2]]
+            lap += -m2 + 16.0 * m1 - 30.0 * u[i, j, k] + 16.0 * p1 - p2
+        lap /= 12.0 * h * h
+        worst = max(worst, abs(lap - fg[i, j, k]))
+        terms = max(terms, 90.0 * abs(u[i, j, k]) / (12.0 * h * h))
+    # the solve stops at ||r - L phi|| <= rel_resid ||r||, which bounds every row;
+    # the host evaluation adds rounding of the O(phi / h^2) terms
+    bound = st.rel_resid * rnorm + 1e-13 * terms
+    assert worst <= bound, (worst, st.rel_resid, rnorm, terms)
+
+
+def test_fullsize_matches_manufactured_solution(solved):
+    st, rc, f, phi, kind, typ, _ = solved
+    u = phi.reshape(N, N, N)
+    h = 1.0 / N
+    k3 = kind.reshape(N, N, N)
+    rng = np.random.default_rng(11)
+    err = 0.0
+    count = 0
+    while count < 4000:
+        i, j, k = rng.integers(0, N, 3)
+        if k3[i, j, k] != 1:  # full cells only: their exact average has a closed form
+            continue
+        err = max(err, abs(u[i, j, k] - exact_average(i, j, k, h)))
+        count += 1
+    assert err < 1e-6, err

@@ -267,3 +267,21 @@ def test_smo1_tiles_tuned(pair):
     cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4)}
     for m in range(len(H.levels) - 1):
         assert tuple(S.info.jacobi_block[m]) in cands
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_trilinear_prolongation_solve(pair, krylov):
+    """The trilinear prolongation option changes only the V-cycle, not the
+    discrete system: the solve reaches the oracle's converged solution."""
+    from paper_2410_05865_gb300 import ccmg
+    S, H, (f, gb, gp), r_or, prob = pair
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, prolong=1, krylov=krylov)
+    lv = H.levels[0]
+    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    assert rc == 0 and st.rel_resid < 1e-10
+    ref, hist, it = H.multigrid(r_or, eps=1e-10)
+    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
+    if krylov == 0:
+        assert st.iters < it  # fewer V-cycles than with the piecewise-constant prolongation
+    K.close()

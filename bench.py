@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--prolong", type=int, default=1,
                     help="0 the paper's piecewise-constant prolongation; 1 trilinear cell-centred")
+    ap.add_argument("--restriction", type=int, default=1,
+                    help="0 the paper's 2^-3 sum over the children; 1 full weighting")
     ap.add_argument("--no-fp64-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape-bc", default="dirichlet", choices=["dirichlet", "neumann"],
@@ -254,7 +256,8 @@ def run_ours(args):
     prob = problem(W, n, args)
     t0 = time.time()
     solver_kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n,
-                     krylov_restart=args.restart, max_iter=2000, prolong=args.prolong)
+                     krylov_restart=args.restart, max_iter=2000, prolong=args.prolong,
+                     restriction=args.restriction)
     S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **solver_kw)
     setup_s = time.time() - t0
     stream = torch.cuda.Stream()
@@ -376,6 +379,8 @@ def run_ours(args):
                        "outer": ["Alg. Multigrid", f"GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
                        "prolongation": ["piecewise constant (the paper's Prolong)",
                                         "trilinear cell-centred over coarse phi1 cells"][args.prolong],
+                       "restriction": ["2^-3 sum over the phi1 children (the paper's Restrict)",
+                                       "full weighting (transpose of trilinear / 8)"][args.restriction],
                        "plain_fp64_same_solver": fp64,
                        "setup_s": round(setup_s, 1), "parallelism": f"replicas x{world}",
                        "l2": "no flush: working set of several GB > 129 MB L2"},
@@ -409,7 +414,7 @@ def run_batch(args):
     world, rank, local = dist_init(args)
     torch.cuda.set_device(local)
     kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=16, krylov_restart=args.restart,
-              max_iter=2000, prolong=args.prolong)
+              max_iter=2000, prolong=args.prolong, restriction=args.restriction)
     t0 = time.time()
     probs, solvers, inputs, phis, skipped = [], [], [], [], []
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()

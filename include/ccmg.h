@@ -96,6 +96,9 @@ typedef struct {
   int prolong;       /* coarse-grid correction: 0 the paper's piecewise-constant
                         prolongation (Prolong); 1 trilinear cell-centred weights from
                         the 8 nearest coarse phi1 cells (0) */
+  int restriction;   /* residual restriction: 0 the paper's 2^-3 sum over the phi1
+                        children (Restrict); 1 full weighting, the transpose of the
+                        trilinear prolongation over 4 x 4 x 4 fine cells / 8 (0) */
 } cc_params;
 
 typedef struct {

@@ -45,7 +45,8 @@ class cc_params(C.Structure):
                 ("rel_tol", C.c_double), ("min_coarse_n", C.c_int), ("max_levels", C.c_int),
                 ("use_graph", C.c_int), ("lu_leaf", C.c_int), ("host_threads", C.c_int),
                 ("krylov", C.c_int), ("krylov_restart", C.c_int), ("precision", C.c_int),
-                ("lu_schedule", C.c_int), ("krylov_cgs", C.c_int), ("prolong", C.c_int)]
+                ("lu_schedule", C.c_int), ("krylov_cgs", C.c_int), ("prolong", C.c_int),
+                ("restriction", C.c_int)]
 
 
 class cc_stats(C.Structure):

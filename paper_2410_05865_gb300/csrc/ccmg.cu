@@ -245,6 +245,46 @@ __global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T
   coarse[(a * nc + b) * nc + c] = T(0.125) * acc;
 }
 
+// Full-weighting restriction, an option beside the paper's 2^-3 sum: the
+// residual s - L phi of the phi1 cells (zero elsewhere) is formed once on the
+// fine grid (k_resid_grid), then coarse[I] takes the transpose of the
+// trilinear prolongation divided by 8: weights (1,3,3,1)/8 per axis over the
+// 4 x 4 x 4 fine cells around I.
+template <class T>
+__global__ void k_resid_grid(const T* __restrict__ phi, const T* __restrict__ s, T* __restrict__ out,
+                             const uint8_t* __restrict__ typ, StencilP P) {
+  const int n = P.n;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const int idx = (i * n + j) * n + k;
+  out[idx] = typ[idx] == 1 ? s[idx] - apply_regular<T>(phi, i, j, k, P) : T(0);
+}
+
+template <class T>
+__global__ void k_restrict_fw(const T* __restrict__ r, T* __restrict__ coarse, int n) {
+  const int nc = n / 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y, a = blockIdx.z;
+  if (c >= nc) return;
+  const T w[4] = {T(1) / T(8), T(3) / T(8), T(3) / T(8), T(1) / T(8)};
+  T acc = T(0);
+  for (int u = 0; u < 4; ++u) {
+    const int i = 2 * a - 1 + u;
+    if (i < 0 || i >= n) continue;
+    for (int v = 0; v < 4; ++v) {
+      const int j = 2 * b - 1 + v;
+      if (j < 0 || j >= n) continue;
+      const T wuv = w[u] * w[v];
+      const int row = (i * n + j) * n;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = 2 * c - 1 + t;
+        if (k >= 0 && k < n) acc += wuv * w[t] * r[row + k];
+      }
+    }
+  }
+  coarse[(a * nc + b) * nc + c] = acc;
+}
+
 // phi1 cells += the parent's correction, taken only from parents that are phi1
 // cells of the coarse level (a coarse phi2 cell prolongates no correction).
 template <class T>
@@ -1177,10 +1217,16 @@ void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double
 }
 
 template <class T>
-void restrict_resid(cc_solver* S, DevLevel& L, const T* phi, const T* s, T* coarse) {
+void restrict_resid(cc_solver* S, DevLevel& L, const T* phi, const T* s, T* coarse, T* tmp = nullptr) {
   const int block = 256;
-  ProfScope ps(S, P_RESTRICT, (2.0 * sizeof(T) + 1.0 + sizeof(T) / 8.0) * L.N);
   (void)block;
+  if (S->prm.restriction == 1 && tmp) {
+    ProfScope ps(S, P_RESTRICT, (4.0 * sizeof(T) + 1.0 + sizeof(T) / 8.0) * L.N, 2);
+    k_resid_grid<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(phi, s, tmp, L.typ, L.P);
+    k_restrict_fw<T><<<grid3(L.n / 2, block3(L.n / 2)), block3(L.n / 2), 0, S->stream>>>(tmp, coarse, L.n);
+    return;
+  }
+  ProfScope ps(S, P_RESTRICT, (2.0 * sizeof(T) + 1.0 + sizeof(T) / 8.0) * L.N);
   k_restrict<T><<<grid3(L.n / 2, block3(L.n / 2)), block3(L.n / 2), 0, S->stream>>>(phi, s, coarse, L.typ, L.P);
 }
 
@@ -1214,7 +1260,7 @@ void vcycle_rec(cc_solver* S, int m, const T* s, T* e) {
     lu_solve<T>(S, L.lu, s, cur);
   }
   DevLevel& Cl = S->lev[m + 1];
-  restrict_resid<T>(S, L, cur, s, Cl.bs<T>());
+  restrict_resid<T>(S, L, cur, s, Cl.bs<T>(), oth);
   vcycle_rec<T>(S, m + 1, Cl.bs<T>(), Cl.be<T>());
   prolong<T>(S, m, Cl.be<T>(), cur);
   for (int it = 0; it < S->prm.nu2; ++it) {
@@ -1654,6 +1700,7 @@ void cc_default_params(cc_params* p) {
   p->lu_schedule = 0;
   p->krylov_cgs = 0;
   p->prolong = 0;
+  p->restriction = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1704,7 +1751,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
       S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
-      S->prm.prolong < 0 || S->prm.prolong > 1) {
+      S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }

@@ -269,13 +269,16 @@ def test_smo1_tiles_tuned(pair):
         assert tuple(S.info.jacobi_block[m]) in cands
 
 
+@pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("krylov", [0, 1])
-def test_trilinear_prolongation_solve(pair, krylov):
-    """The trilinear prolongation option changes only the V-cycle, not the
-    discrete system: the solve reaches the oracle's converged solution."""
+def test_trilinear_prolongation_solve(pair, krylov, restriction):
+    """The trilinear prolongation and full-weighting restriction options change
+    only the V-cycle, not the discrete system: the solve reaches the oracle's
+    converged solution."""
     from paper_2410_05865_gb300 import ccmg
     S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, prolong=1, krylov=krylov)
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, prolong=1, krylov=krylov,
+                    restriction=restriction)
     lv = H.levels[0]
     phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
     st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)

@@ -376,7 +376,8 @@ def run_ours(args):
                                      "fp32 grid work; fp64 LU-corrections, bottom solve, outer residual",
                                      "fp32 grid work and LU-correction factors; fp64 PLG rows, bottom solve, "
                                      "outer residual"][args.precision],
-                       "outer": ["Alg. Multigrid", f"GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
+                       "outer": ["Alg. Multigrid",
+                                 f"flexible GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
                        "prolongation": ["piecewise constant (the paper's Prolong)",
                                         "trilinear cell-centred over coarse phi1 cells"][args.prolong],
                        "restriction": ["2^-3 sum over the phi1 children (the paper's Restrict)",

@@ -99,6 +99,10 @@ typedef struct {
   int restriction;   /* residual restriction: 0 the paper's 2^-3 sum over the phi1
                         children (Restrict); 1 full weighting, the transpose of the
                         trilinear prolongation over 4 x 4 x 4 fine cells / 8 (0) */
+  int krylov_flexible;/* 1: flexible GMRES, which keeps the preconditioned vectors and
+                        updates phi with them (no extra V-cycle per restart, and exact
+                        for an FP32 V-cycle that is not quite a fixed linear map);
+                        0: GMRES that applies the V-cycle again to the combined basis (1) */
 } cc_params;
 
 typedef struct {

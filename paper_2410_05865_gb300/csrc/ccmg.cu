@@ -762,6 +762,7 @@ struct cc_solver {
   double* khdots = nullptr; // pinned copy
   double* kzero = nullptr;  // a zero grid array
   double* kin = nullptr;    // fixed input of the captured preconditioner
+  double* kZ = nullptr;     // flexible GMRES: the m preconditioned vectors
   int km = 0;
   // profiling
   bool prof = false;
@@ -1504,6 +1505,7 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     if ((st = dalloc(S, &S->kw, N))) return st;
     if ((st = dalloc(S, &S->kzero, N))) return st;
     if ((st = dalloc(S, &S->kin, N))) return st;
+    if (S->prm.krylov_flexible && (st = dalloc(S, &S->kZ, (size_t)m * N))) return st;
     drop_graph(S);
     if ((st = dalloc(S, &S->kdots, (size_t)2 * (m + 2)))) return st;
     if (!S->khdots) CK(cudaMallocHost((void**)&S->khdots, sizeof(double) * 2 * 66));
@@ -1555,6 +1557,8 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       cc_status pst = apply_prec(S, vj);  // z = M v_j
       if (pst) return pst;
       ++cycles;
+      if (S->prm.krylov_flexible)  // keep z_j: the update is phi += Z y with the same z_j
+        CK(cudaMemcpyAsync(S->kZ + (long long)j * N, L.e, N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream));
       // w = A z = -(0 - A z)
       resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
       {
@@ -1607,14 +1611,20 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       y[i] = s / H[(size_t)i * m + i];
     }
     CK(cudaMemcpyAsync(S->kdots + m + 2, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, S->stream));
-    {
-      ProfScope ps(S, P_KRYLOV, (8.0 * k + 8.0) * N);
-      k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
+    if (S->prm.krylov_flexible) {  // phi += Z y (flexible GMRES: no V-cycle after the solve)
+      ProfScope ps(S, P_KRYLOV, (8.0 * k + 32.0) * N, 2);
+      k_combine<<<grid, block, 0, S->stream>>>(S->kw, S->kZ, S->kdots + m + 2, k, N);
+      k_axpy<<<grid, block, 0, S->stream>>>(S->phi, S->kw, N);
+    } else {
+      {
+        ProfScope ps(S, P_KRYLOV, (8.0 * k + 8.0) * N);
+        k_combine<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots + m + 2, k, N);
+      }
+      cc_status pst = apply_prec(S, S->kw);
+      if (pst) return pst;
+      ++cycles;
+      k_axpy<<<grid, block, 0, S->stream>>>(S->phi, L.e, N);
     }
-    cc_status pst = apply_prec(S, S->kw);
-    if (pst) return pst;
-    ++cycles;
-    k_axpy<<<grid, block, 0, S->stream>>>(S->phi, L.e, N);
   }
   if (S->nabs) k_absorbed<<<grid_for(S, S->nabs, 128), 128, 0, S->stream>>>(S->phi, S->nabs, S->a_cell, S->a_own);
   CK(cudaGetLastError());
@@ -1701,6 +1711,7 @@ void cc_default_params(cc_params* p) {
   p->krylov_cgs = 0;
   p->prolong = 0;
   p->restriction = 0;
+  p->krylov_flexible = 1;
 }
 
 const char* cc_status_str(cc_status st) {

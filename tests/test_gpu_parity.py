@@ -205,12 +205,15 @@ def test_solve_host_buffers(pair):
     assert np.abs(phi - phi_d.cpu().numpy()).max() < 1e-12 * np.abs(phi).max()
 
 
-def test_gmres_acceleration(pair):
-    """GMRES right-preconditioned by the same V-cycle reaches the same discrete
-    solution (the oracle's converged Alg. Multigrid) in fewer V-cycles."""
+@pytest.mark.parametrize("flexible", [0, 1])
+def test_gmres_acceleration(pair, flexible):
+    """GMRES right-preconditioned by the same V-cycle (plain, or flexible with the
+    preconditioned vectors kept) reaches the same discrete solution (the
+    oracle's converged Alg. Multigrid) in fewer V-cycles."""
     from paper_2410_05865_gb300 import ccmg
     S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, krylov=1, krylov_restart=30)
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, krylov=1, krylov_restart=30,
+                    krylov_flexible=flexible)
     lv = H.levels[0]
     phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
     st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)

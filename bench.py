@@ -58,6 +58,8 @@ def parse():
                     help="0 the paper's piecewise-constant prolongation; 1 trilinear cell-centred")
     ap.add_argument("--restriction", type=int, default=1,
                     help="0 the paper's 2^-3 sum over the children; 1 full weighting")
+    ap.add_argument("--cgs", type=int, default=1,
+                    help="GMRES orthogonalisation: 0 modified, 1 classical Gram-Schmidt (two fused passes)")
     ap.add_argument("--no-fp64-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape-bc", default="dirichlet", choices=["dirichlet", "neumann"],
@@ -257,7 +259,7 @@ def run_ours(args):
     t0 = time.time()
     solver_kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n,
                      krylov_restart=args.restart, max_iter=2000, prolong=args.prolong,
-                     restriction=args.restriction)
+                     restriction=args.restriction, krylov_cgs=args.cgs)
     S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **solver_kw)
     setup_s = time.time() - t0
     stream = torch.cuda.Stream()
@@ -377,7 +379,8 @@ def run_ours(args):
                                      "fp32 grid work and LU-correction factors; fp64 PLG rows, bottom solve, "
                                      "outer residual"][args.precision],
                        "outer": ["Alg. Multigrid",
-                                 f"flexible GMRES({args.restart}) preconditioned by the V-cycle"][args.krylov],
+                                 f"flexible GMRES({args.restart}) preconditioned by the V-cycle, "
+                                 f"{['modified', 'classical'][args.cgs]} Gram-Schmidt"][args.krylov],
                        "prolongation": ["piecewise constant (the paper's Prolong)",
                                         "trilinear cell-centred over coarse phi1 cells"][args.prolong],
                        "restriction": ["2^-3 sum over the phi1 children (the paper's Restrict)",
@@ -415,7 +418,7 @@ def run_batch(args):
     world, rank, local = dist_init(args)
     torch.cuda.set_device(local)
     kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=16, krylov_restart=args.restart,
-              max_iter=2000, prolong=args.prolong, restriction=args.restriction)
+              max_iter=2000, prolong=args.prolong, restriction=args.restriction, krylov_cgs=args.cgs)
     t0 = time.time()
     probs, solvers, inputs, phis, skipped = [], [], [], [], []
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()

@@ -2,10 +2,12 @@
 //
 // Data layout in HBM (per level m, n = n_m):
 //   grid arrays   n^3 doubles, index (i*n + j)*n + k (k fastest): phi, s, e, tmp
+//                 (and FP32 copies for the mixed-precision V-cycle)
 //   typ           n^3 bytes: 0 none, 1 phi1, 2 phi2
 //   phi2 rows     CSR over the phi2 cells (grid-index columns), FP64
-//   LU factors    per supernode: inv(L_ss), inv(U_ss), L_{struct,s}, U_{s,struct}
-//                 (row-major FP64), plus row tasks grouped by tree height
+//   LU factors    per supernode the block-elimination matrices G, W, V
+//                 (column-major, FP64 or FP32), plus warp tasks grouped by tree
+//                 height for each sweep
 // The regular 13-point rows (eq. regularLaplaceDiscretization, box ghosts
 // eliminated) are not stored: each kernel evaluates them from a per-level table
 // of 1-D rows by position class {0, 1, interior, n-2, n-1}.

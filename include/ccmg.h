@@ -201,6 +201,17 @@ cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_s
 /* ---- hot-path steps, device pointers, grid arrays of `level`, FP64 ------- */
 /* out = s - L phi on phi1 rows (and on phi2 rows if phi2_rows != 0, else 0). */
 cc_status cc_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* out, int phi2_rows);
+/* out = rhs - L z on phi1 rows (rhs may be NULL: 0), 0 on every other cell, for
+ * z given in FP32 (a grid array of n^3 floats, device memory, caller-owned).
+ * The interior rows of eq. regularLaplaceDiscretization are summed exactly in
+ * 64-bit fixed point on the exponent of the row's largest value (a value more
+ * than 2^31 times smaller keeps its bits down to 2^-54 of the largest) and
+ * rounded once to FP64; rows within two cells of the box are evaluated in FP64.
+ * The same kernel applies the operator in GMRES (params.krylov = 1; not in
+ * the paper) to the output of an FP32 V-cycle (params.precision >= 1).  Errors: CC_ERR_INVALID_ARG for a
+ * NULL solver, z or out, or a level out of range; an Inf or NaN among a
+ * row's values makes that row non-finite. */
+cc_status cc_residual_f32(cc_solver* s, int level, const float* z, const double* rhs, double* out);
 /* SMO-1: phi_out = phi_in + omega D^{-1} (rhs - L phi_in) on phi1, copy elsewhere. */
 cc_status cc_jacobi(cc_solver* s, int level, const double* phi_in, const double* rhs, double* phi_out);
 /* SMO-2 in place: phi2 <- L22^{-1} (rhs2 - L21 phi1). */

@@ -83,6 +83,7 @@ SIGNATURES = {
     "cc_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_int, C.POINTER(cc_stats)]),
     "cc_solve_r": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(cc_stats)]),
     "cc_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
+    "cc_residual_f32": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_jacobi": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_solve_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                  C.POINTER(_P), C.c_int, _P, C.POINTER(C.c_int)]),
@@ -268,6 +269,12 @@ class Solver:
     # ------------------------------------------------------ hot-path steps
     def residual(self, level, phi, s, out, phi2_rows=True):
         self._check(lib().cc_residual(self._h, level, _ptr(phi), _ptr(s), _ptr(out), int(phi2_rows)), "cc_residual")
+
+    def residual_f32(self, level, z, s, out):
+        """out = s - L z on phi1 rows (s None: 0) for a float32 grid array z;
+        interior rows summed exactly in fixed point."""
+        self._check(lib().cc_residual_f32(self._h, level, _ptr(z), _ptr(s) if s is not None else None,
+                                          _ptr(out)), "cc_residual_f32")
 
     def jacobi(self, level, phi_in, s, phi_out):
         self._check(lib().cc_jacobi(self._h, level, _ptr(phi_in), _ptr(s), _ptr(phi_out)), "cc_jacobi")

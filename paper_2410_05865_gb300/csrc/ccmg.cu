@@ -106,9 +106,10 @@ __device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1,
   }
 }
 
-// (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32).
-template <class T>
-__device__ __forceinline__ T apply_regular(const T* __restrict__ phi, int i, int j, int k, const StencilP& P) {
+// (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32); phi
+// may be stored in a narrower type S (FP32 values evaluated in FP64).
+template <class T, class S = T>
+__device__ __forceinline__ T apply_regular(const S* __restrict__ phi, int i, int j, int k, const StencilP& P) {
   // 32-bit indices: cc_setup limits n to 1024, so n^3 < 2^31
   const int n = P.n;
   const int nn = n * n;
@@ -194,6 +195,169 @@ __global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, co
     }
   }
   *reinterpret_cast<V2*>(phi_out + idx) = res;
+}
+
+// The interior row, exactly, for values held in FP32.  An FP32 value is
+// m 2^(e-150) with an integer m < 2^24 (e = 1 and no implicit bit for a
+// subnormal).  In units of 2^(emax-181), emax the largest e among the row's 13
+// values, each value becomes an integer below 2^55 (exact unless it is more than
+// 2^31 times smaller than the largest, when only its bits below the unit are
+// dropped), and 16 sum_{|o|=1} - sum_{|o|=2} - 90 c, at most 192 such integers,
+// stays below 2^63.  The row sum is therefore formed exactly in 64-bit integers
+// and rounded once, on conversion to FP64; one product with 2^(emax-181) / (12 h^2)
+// (built exactly by adding to the exponent field) finishes the row, where the
+// FP64 row costs 14 FP64 operations (the slow pipe on this GPU).  For FP32
+// inputs the FP64 row is nearly always exact too: the point is speed, at no
+// loss of accuracy for values within 2^31 of each other.
+__device__ __forceinline__ long long fx_unit(unsigned int m, int e, unsigned int b, int emax) {
+  const int sh = emax - e;
+  long long q;
+  if (sh <= 31)
+    q = (long long)m << (31 - sh);
+  else
+    q = sh - 31 < 24 ? (long long)(m >> (sh - 31)) : 0;
+  return (b >> 31) ? -q : q;
+}
+
+// The row sum 16 sum_{|o|=1} - sum_{|o|=2} - 90 c in units of 2^(emax-181); emax = 255
+// flags an Inf or NaN among the values.
+__device__ __forceinline__ long long fx_row(const unsigned int (&v)[13], int& emax_out) {
+  int e[13];
+  int emax = 1, emin = 255;
+#pragma unroll
+  for (int t = 0; t < 13; ++t) {
+    e[t] = max((int)((v[t] >> 23) & 0xFF), 1);
+    emax = max(emax, e[t]);
+    emin = min(emin, e[t]);
+  }
+  emax_out = emax;
+  if (emax == 255) return 0;
+  long long s1 = 0, s2 = 0, c;
+  if (emax - emin <= 31) {
+    // the usual case: every value is its signed 25-bit integer shifted left
+    long long q[13];
+#pragma unroll
+    for (int t = 0; t < 13; ++t) {
+      const unsigned int b = v[t];
+      const int m = (int)((b & 0x7FFFFFu) | ((b & 0x7F800000u) ? 0x800000u : 0u));
+      const long long sm = (b >> 31) ? -(long long)m : (long long)m;
+      q[t] = (long long)((unsigned long long)sm << (31 - emax + e[t]));
+    }
+    s1 = ((q[1] + q[2]) + (q[3] + q[4])) + (q[5] + q[6]);
+    s2 = ((q[7] + q[8]) + (q[9] + q[10])) + (q[11] + q[12]);
+    c = q[0];
+  } else {
+    unsigned int m[13];
+#pragma unroll
+    for (int t = 0; t < 13; ++t) m[t] = (v[t] & 0x7FFFFFu) | ((v[t] & 0x7F800000u) ? 0x800000u : 0u);
+#pragma unroll
+    for (int t = 1; t <= 6; ++t) s1 += fx_unit(m[t], e[t], v[t], emax);
+#pragma unroll
+    for (int t = 7; t <= 12; ++t) s2 += fx_unit(m[t], e[t], v[t], emax);
+    c = fx_unit(m[0], e[0], v[0], emax);
+  }
+  return 16 * s1 - s2 - 90 * c;
+}
+
+// f 2^(emax-181), exact (only the exponent field changes) for |f| = 1/(12 h^2),
+// between 0.08 and 1e5 for n <= 1024, so the product stays a normal FP64 number
+__device__ __forceinline__ double fx_scale(double f, int emax) {
+  return __longlong_as_double(__double_as_longlong(f) + ((long long)(emax - 181) << 52));
+}
+
+// out = s - L z on the phi1 rows (s = nullptr: 0), 0 elsewhere, for z held in
+// FP32, in two launches whose warps each take one path: k_resid1_z32_in over the
+// cells two or more cells from the box (fixed point, fx_row) and
+// k_resid1_z32_shell over the n^3 - (n-4)^3 cells nearer the box (FP64).  A warp
+// mixing the two would issue the FP64 path, at the FP64 pipe's rate, for its
+// few box lanes.
+__global__ void k_resid1_z32_in(const float* __restrict__ z, const double* __restrict__ s, double* __restrict__ out,
+                                const uint8_t* __restrict__ typ, StencilP P) {
+  const int n = P.n;
+  const int k = 2 + blockIdx.x * blockDim.x + threadIdx.x, j = 2 + blockIdx.y, i = 2 + blockIdx.z;
+  if (k >= n - 2) return;
+  const int nn = n * n;
+  const int idx = (i * n + j) * n + k;
+  double r = 0.0;
+  if (typ[idx] == 1) {
+    const unsigned int* b = reinterpret_cast<const unsigned int*>(z);
+    const unsigned int v[13] = {b[idx],          b[idx + nn],     b[idx - nn],     b[idx + n],     b[idx - n],
+                                b[idx + 1],      b[idx - 1],      b[idx + 2 * nn], b[idx - 2 * nn], b[idx + 2 * n],
+                                b[idx - 2 * n], b[idx + 2],      b[idx - 2]};
+    int emax;
+    const double acc = __ll2double_rn(fx_row(v, emax));
+    const double neg = fx_scale(-P.inv12h2, emax);  // -(L z) = acc * neg
+    if (emax == 255)
+      r = __longlong_as_double(0x7FF8000000000000LL);
+    else
+      r = s ? __fma_rn(acc, neg, s[idx]) : acc * neg;
+  }
+  out[idx] = r;
+}
+
+// The t-th cell within two cells of the box (n >= 4): the planes i in {0,1,n-2,n-1},
+// then the rows j in {0,1,n-2,n-1} of the other planes, then the cells
+// k in {0,1,n-2,n-1} of the remaining rows.
+__device__ __forceinline__ int edge4(int x, int n) { return x < 2 ? x : n - 4 + x; }
+__device__ __forceinline__ void shell_cell(int t, int n, int& i, int& j, int& k) {
+  const int m = n - 4;
+  const int a = 4 * n * n, b = 4 * m * n;
+  if (t < a) {
+    const int r = t % (n * n);
+    i = edge4(t / (n * n), n);
+    j = r / n;
+    k = r % n;
+  } else if (t < a + b) {
+    t -= a;
+    const int r = t % (4 * n);
+    i = 2 + t / (4 * n);
+    j = edge4(r / n, n);
+    k = r % n;
+  } else {
+    t -= a + b;
+    const int r = t % (4 * m);
+    i = 2 + t / (4 * m);
+    j = 2 + r / 4;
+    k = edge4(r % 4, n);
+  }
+}
+
+__global__ void k_resid1_z32_shell(const float* __restrict__ z, const double* __restrict__ s,
+                                   double* __restrict__ out, const uint8_t* __restrict__ typ, StencilP P, int count) {
+  const int n = P.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    int i, j, k;
+    shell_cell(t, n, i, j, k);
+    const int idx = (i * n + j) * n + k;
+    out[idx] = typ[idx] == 1 ? (s ? s[idx] : 0.0) - apply_regular<double, float>(z, i, j, k, P) : 0.0;
+  }
+}
+
+// The same on one launch over all cells (grids too small for the split, n < 8).
+__global__ void k_resid1_z32(const float* __restrict__ z, const double* __restrict__ s, double* __restrict__ out,
+                             const uint8_t* __restrict__ typ, StencilP P) {
+  const int n = P.n;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= n) return;
+  const int nn = n * n;
+  const int idx = (i * n + j) * n + k;
+  double r = 0.0;
+  if (typ[idx] == 1) {
+    double lz;
+    if (i >= 2 && i < n - 2 && j >= 2 && j < n - 2 && k >= 2 && k < n - 2) {
+      const unsigned int* b = reinterpret_cast<const unsigned int*>(z);
+      const unsigned int v[13] = {b[idx],          b[idx + nn],     b[idx - nn],    b[idx + n],    b[idx - n],
+                                  b[idx + 1],      b[idx - 1],      b[idx + 2 * nn], b[idx - 2 * nn], b[idx + 2 * n],
+                                  b[idx - 2 * n], b[idx + 2],     b[idx - 2]};
+      int emax;
+      const double acc = __ll2double_rn(fx_row(v, emax));
+      lz = emax == 255 ? __longlong_as_double(0x7FF8000000000000LL) : acc * fx_scale(P.inv12h2, emax);
+    } else {
+      lz = apply_regular<double, float>(z, i, j, k, P);
+    }
+    r = (s ? s[idx] : 0.0) - lz;
+  }
+  out[idx] = r;
 }
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
@@ -1219,6 +1383,25 @@ void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double
   }
 }
 
+// out = s - L z for a z held in FP32 (s = nullptr: 0); with z64 (its exact FP64
+// copy) the phi2 rows too, else 0 there
+void resid_z32(cc_solver* S, DevLevel& L, const float* z, const double* z64, const double* s, double* out) {
+  if (L.n >= 8) {
+    const int m = L.n - 4, shell = L.n * L.n * L.n - m * m * m;
+    ProfScope ps(S, P_RESID1, (s ? 21.0 : 13.0) * L.N, 2);
+    k_resid1_z32_in<<<grid3(m, block3(m)), block3(m), 0, S->stream>>>(z, s, out, L.typ, L.P);
+    k_resid1_z32_shell<<<grid_for(S, shell, 128), 128, 0, S->stream>>>(z, s, out, L.typ, L.P, shell);
+  } else {
+    ProfScope ps(S, P_RESID1, (s ? 21.0 : 13.0) * L.N);
+    k_resid1_z32<<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(z, s, out, L.typ, L.P);
+  }
+  if (z64 && L.n2 > 0) {
+    ProfScope ps(S, P_RESID2, 12.0 * L.p2_nnz);
+    k_resid2<<<grid_for(S, L.n2, 256), 256, 0, S->stream>>>(z64, s ? s : S->kzero, out, L.n2, L.p2_cell, L.p2_ptr,
+                                                             L.p2_col, L.p2_val, nullptr);
+  }
+}
+
 template <class T>
 void restrict_resid(cc_solver* S, DevLevel& L, const T* phi, const T* s, T* coarse, T* tmp = nullptr) {
   const int block = 256;
@@ -1561,8 +1744,12 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
       ++cycles;
       if (S->prm.krylov_flexible)  // keep z_j: the update is phi += Z y with the same z_j
         CK(cudaMemcpyAsync(S->kZ + (long long)j * N, L.e, N * sizeof(double), cudaMemcpyDeviceToDevice, S->stream));
-      // w = A z = -(0 - A z)
-      resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
+      // w = A z = -(0 - A z); an FP32 V-cycle's z is exact in FP32 (L.e is its FP64
+      // copy), so its phi1 rows take the exact fixed-point sums
+      if (S->prm.precision >= 1)
+        resid_z32(S, L, L.e32, L.e, nullptr, S->kw);
+      else
+        resid(S, L, L.e, S->kzero, S->kw, true, nullptr);
       {
         // modified Gram-Schmidt: per basis vector a dot (2 reads) and an update (2 reads, 1 write)
         ProfScope ps(S, P_KRYLOV,
@@ -2192,6 +2379,16 @@ cc_status cc_residual(cc_solver* S, int level, const double* phi, const double* 
   cc_status st = check_level(S, level);
   if (st) return st;
   resid(S, S->lev[level], phi, rhs, out, phi2_rows != 0, nullptr);
+  CK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status cc_residual_f32(cc_solver* S, int level, const float* z, const double* rhs, double* out) {
+  if (!S || !z || !out) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = check_level(S, level);
+  if (st) return st;
+  resid_z32(S, S->lev[level], z, nullptr, rhs, out);
   CK(cudaGetLastError());
   return CC_OK;
 }

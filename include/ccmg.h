@@ -205,7 +205,7 @@ cc_status cc_residual(cc_solver* s, int level, const double* phi, const double* 
  * z given in FP32 (a grid array of n^3 floats, device memory, caller-owned).
  * The interior rows of eq. regularLaplaceDiscretization are summed exactly in
  * 64-bit fixed point on the exponent of the row's largest value (a value more
- * than 2^31 times smaller keeps its bits down to 2^-54 of the largest) and
+ * than 2^30 times smaller keeps its bits down to 2^-53 of the largest) and
  * rounded once to FP64; rows within two cells of the box are evaluated in FP64.
  * The same kernel applies the operator in GMRES (params.krylov = 1; not in
  * the paper) to the output of an FP32 V-cycle (params.precision >= 1).  Errors: CC_ERR_INVALID_ARG for a

@@ -199,70 +199,75 @@ __global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, co
 
 // The interior row, exactly, for values held in FP32.  An FP32 value is
 // m 2^(e-150) with an integer m < 2^24 (e = 1 and no implicit bit for a
-// subnormal).  In units of 2^(emax-181), emax the largest e among the row's 13
-// values, each value becomes an integer below 2^55 (exact unless it is more than
-// 2^31 times smaller than the largest, when only its bits below the unit are
+// subnormal).  In units of 2^(emax-180), emax the largest e among the row's 13
+// values, each value becomes an integer below 2^54 (exact unless it is more than
+// 2^30 times smaller than the largest, when only its bits below the unit are
 // dropped), and 16 sum_{|o|=1} - sum_{|o|=2} - 90 c, at most 192 such integers,
-// stays below 2^63.  The row sum is therefore formed exactly in 64-bit integers
-// and rounded once, on conversion to FP64; one product with 2^(emax-181) / (12 h^2)
+// stays below 2^62.  The row sum is therefore formed exactly in 64-bit integers
+// and rounded once, on conversion to FP64; one product with 2^(emax-180) / (12 h^2)
 // (built exactly by adding to the exponent field) finishes the row, where the
 // FP64 row costs 14 FP64 operations (the slow pipe on this GPU).  For FP32
 // inputs the FP64 row is nearly always exact too: the point is speed, at no
-// loss of accuracy for values within 2^31 of each other.
+// loss of accuracy for values within 2^30 of each other.
 __device__ __forceinline__ long long fx_unit(unsigned int m, int e, unsigned int b, int emax) {
   const int sh = emax - e;
   long long q;
-  if (sh <= 31)
-    q = (long long)m << (31 - sh);
+  if (sh <= 30)
+    q = (long long)m << (30 - sh);
   else
-    q = sh - 31 < 24 ? (long long)(m >> (sh - 31)) : 0;
+    q = sh - 30 < 24 ? (long long)(m >> (sh - 30)) : 0;
   return (b >> 31) ? -q : q;
 }
 
-// The row sum 16 sum_{|o|=1} - sum_{|o|=2} - 90 c in units of 2^(emax-181); emax = 255
+// The row sum 16 sum_{|o|=1} - sum_{|o|=2} - 90 c in units of 2^(emax-180); emax = 255
 // flags an Inf or NaN among the values.
 __device__ __forceinline__ long long fx_row(const unsigned int (&v)[13], int& emax_out) {
-  int e[13];
-  int emax = 1, emin = 255;
+  int er[13];
+  int emax = 0, emin = 255;
 #pragma unroll
   for (int t = 0; t < 13; ++t) {
-    e[t] = max((int)((v[t] >> 23) & 0xFF), 1);
-    emax = max(emax, e[t]);
-    emin = min(emin, e[t]);
+    er[t] = (v[t] >> 23) & 0xFF;
+    emax = max(emax, er[t]);
+    emin = min(emin, er[t]);
   }
-  emax_out = emax;
-  if (emax == 255) return 0;
-  long long s1 = 0, s2 = 0, c;
-  if (emax - emin <= 31) {
-    // the usual case: every value is its signed 25-bit integer shifted left
-    long long q[13];
+  long long s1 = 0, s2 = 0, c = 0;
+  if (emin >= 1 && emax < 255 && emax - emin <= 30) {
+    // the usual case (normal values within 2^30): each value's signed 25-bit
+    // integer times 2^(30 - (emax - e)), one widening multiply-add per value
+    int sm[13];
 #pragma unroll
     for (int t = 0; t < 13; ++t) {
-      const unsigned int b = v[t];
-      const int m = (int)((b & 0x7FFFFFu) | ((b & 0x7F800000u) ? 0x800000u : 0u));
-      const long long sm = (b >> 31) ? -(long long)m : (long long)m;
-      q[t] = (long long)((unsigned long long)sm << (31 - emax + e[t]));
+      const int m = (int)((v[t] & 0x7FFFFFu) | 0x800000u);
+      const int sg = (int)v[t] >> 31;  // 0 or -1
+      sm[t] = (m ^ sg) - sg;
     }
-    s1 = ((q[1] + q[2]) + (q[3] + q[4])) + (q[5] + q[6]);
-    s2 = ((q[7] + q[8]) + (q[9] + q[10])) + (q[11] + q[12]);
-    c = q[0];
+#pragma unroll
+    for (int t = 1; t <= 6; ++t) s1 += (long long)sm[t] * (long long)(1 << (30 - emax + er[t]));
+#pragma unroll
+    for (int t = 7; t <= 12; ++t) s2 += (long long)sm[t] * (long long)(1 << (30 - emax + er[t]));
+    c = (long long)sm[0] * (long long)(1 << (30 - emax + er[0]));
   } else {
-    unsigned int m[13];
+    emax = max(emax, 1);
+    emax_out = emax;
+    if (emax == 255) return 0;
 #pragma unroll
-    for (int t = 0; t < 13; ++t) m[t] = (v[t] & 0x7FFFFFu) | ((v[t] & 0x7F800000u) ? 0x800000u : 0u);
-#pragma unroll
-    for (int t = 1; t <= 6; ++t) s1 += fx_unit(m[t], e[t], v[t], emax);
-#pragma unroll
-    for (int t = 7; t <= 12; ++t) s2 += fx_unit(m[t], e[t], v[t], emax);
-    c = fx_unit(m[0], e[0], v[0], emax);
+    for (int t = 0; t < 13; ++t) {
+      const unsigned int m = (v[t] & 0x7FFFFFu) | (er[t] ? 0x800000u : 0u);
+      const long long q = fx_unit(m, max(er[t], 1), v[t], emax);
+      if (t == 0) c = q;
+      else if (t <= 6) s1 += q;
+      else s2 += q;
+    }
+    return 16 * s1 - s2 - 90 * c;
   }
+  emax_out = emax;
   return 16 * s1 - s2 - 90 * c;
 }
 
-// f 2^(emax-181), exact (only the exponent field changes) for |f| = 1/(12 h^2),
+// f 2^(emax-180), exact (only the exponent field changes) for |f| = 1/(12 h^2),
 // between 0.08 and 1e5 for n <= 1024, so the product stays a normal FP64 number
 __device__ __forceinline__ double fx_scale(double f, int emax) {
-  return __longlong_as_double(__double_as_longlong(f) + ((long long)(emax - 181) << 52));
+  return __longlong_as_double(__double_as_longlong(f) + ((long long)(emax - 180) << 52));
 }
 
 // out = s - L z on the phi1 rows (s = nullptr: 0), 0 elsewhere, for z held in
@@ -522,6 +527,39 @@ __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const i
     double v = (double)s[cell[p]];
     for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
     b[p] = (TW)v;
+    x[p] = TW(0);
+  }
+}
+
+// The same for an FP32 grid with no FP64 arithmetic: the row is summed in
+// double-float, an unevaluated pair hi + lo of FP32 numbers.  val is stored as
+// such a pair; val.hi * phi is split exactly into a product and its rounding
+// error by one FMA (the TwoProduct of Ogita, Rump and Oishi, 2005), and the
+// running sum keeps its own rounding errors by Knuth's TwoSum.  The row then
+// carries about 2^-48 of its terms' magnitude in error, far below the FP32
+// phi it is formed from, at a tenth of the FP64 pipe's cost per entry.
+template <class TW>
+__global__ void k_lu_rhs_df(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
+                            const int* __restrict__ ptr, const int* __restrict__ col, const float2* __restrict__ val,
+                            const float* __restrict__ s, const float* __restrict__ phi, unsigned int* __restrict__ bar) {
+  if (bar && blockIdx.x == 0 && threadIdx.x <= kBarGroups) bar[threadIdx.x] = 0u;  // one-launch sweep counters
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    float hi = s[cell[p]], lo = 0.0f;
+    for (int q = ptr[p]; q < ptr[p + 1]; ++q) {
+      const float2 v = val[q];
+      const float z = phi[col[q]];
+      const float ph = __fmul_rn(v.x, z);
+      const float pl = __fmaf_rn(v.y, z, __fmaf_rn(v.x, z, -ph));  // (val.hi z - ph) + val.lo z
+      const float t = __fsub_rn(hi, ph);                           // TwoSum(hi, -ph)
+      const float bv = __fsub_rn(t, hi);
+      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(-ph, bv));
+      hi = t;
+      lo = __fadd_rn(lo, __fsub_rn(err, pl));
+    }
+    if constexpr (sizeof(TW) == 4)
+      b[p] = __fadd_rn(hi, lo);
+    else
+      b[p] = (double)hi + (double)lo;
     x[p] = TW(0);
   }
 }
@@ -844,6 +882,7 @@ struct DevLU {
   int* cell = nullptr;  // ND position -> grid index
   int *rptr = nullptr, *rcol = nullptr;
   double* rval = nullptr;
+  float2* rval2 = nullptr;  // the same values as FP32 pairs hi + lo (FP32-grid right-hand sides)
   long long entries = 0;
   long long rnnz = 0;
 };
@@ -1252,6 +1291,12 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   if ((st = dupload(S, &D.rptr, rp))) return st;
   if ((st = dupload(S, &D.rcol, rc))) return st;
   if ((st = dupload(S, &D.rval, rv))) return st;
+  std::vector<float2> rv2(rv.size());
+  for (size_t q = 0; q < rv.size(); ++q) {
+    const float hi = (float)rv[q];
+    rv2[q] = make_float2(hi, (float)(rv[q] - (double)hi));
+  }
+  if ((st = dupload(S, &D.rval2, rv2))) return st;
   return CC_OK;
 }
 
@@ -1281,8 +1326,12 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
   const bool one = D.coop_grid > 0 && !D.coop_failed;
   {
     ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 2.0 * sizeof(TV) * D.np);
-    k_lu_rhs<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol, D.rval,
-                                                                       s, phi, one ? D.bar : nullptr);
+    if constexpr (sizeof(T) == 4)
+      k_lu_rhs_df<TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol,
+                                                                         D.rval2, s, phi, one ? D.bar : nullptr);
+    else
+      k_lu_rhs<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol,
+                                                                         D.rval, s, phi, one ? D.bar : nullptr);
   }
   // one profiling scope around both sweeps: inside a graph, per-launch event
   // records would cost as much as the short launches they time

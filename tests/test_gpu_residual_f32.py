@@ -5,13 +5,13 @@ kernel.  Its interior rows (eq. regularLaplaceDiscretization,
 (16 sum_{|o|=1} z - sum_{|o|=2} z - 90 z_c) / (12 h^2)) are summed in 64-bit
 fixed point, so they are pinned here against the exact rational value of the
 row, computed on the host with Python fractions from the FP32 inputs:
-* values within a factor 2^31 of each other: the row is exact and rounded
+* values within a factor 2^30 of each other: the row is exact and rounded
   twice (the conversion to FP64 and the product with 1/(12 h^2)), so it
   matches the exact value to 3e-16 relative to the RESULT, here where the
   row cancels to about 1e-4 of its terms (a dropped bit, a wrong shift or
   sign of one value fails this);
-* values spread over 2^140, with zeros and subnormals: values more than 2^31
-  below the row's largest lose only their bits below 2^-54 of it (at most
+* values spread over 2^140, with zeros and subnormals: values more than 2^30
+  below the row's largest lose only their bits below 2^-53 of it (at most
   192 such units per row);
 * an Inf makes the rows that read it non-finite and leaves the others finite.
 All rows, including those near the box (evaluated in FP64), are compared with
@@ -92,8 +92,8 @@ def _check_exact(S, level, z32, rows, spread):
         got = -out[i, j, k]  # out = 0 - L z
         err = abs(Fraction(float(got)) - exact)
         bound = Fraction(3, 10 ** 16) * abs(exact)
-        if spread:  # truncated values: at most 192 units of 2^(emax-181), times 1/(12 h^2)
-            bound += 192 * Fraction(2) ** (_max_exponent(zg, i, j, k) - 181) * Fraction(inv)
+        if spread:  # truncated values: at most 192 units of 2^(emax-180), times 1/(12 h^2)
+            bound += 192 * Fraction(2) ** (_max_exponent(zg, i, j, k) - 180) * Fraction(inv)
         assert err <= bound, (i, j, k, float(err), float(bound), float(exact))
         if exact != 0:
             worst = max(worst, float(err / abs(exact)))

@@ -759,26 +759,40 @@ __global__ void k_combine(double* __restrict__ u, const double* __restrict__ V, 
 // update per basis vector): dots[i] += <w, V_i> for i < k, eight vectors per pass
 // over w (k_mdot), then w -= sum_i h_i V_i with ||w||^2 of the result (k_mupdate).
 constexpr int kMdotVec = 8;
+// one pass of k_mdot over NV basis vectors: exactly NV FP64 FMAs per element (a
+// pass over fewer vectors than kMdotVec does not issue the missing ones)
+template <int NV>
+__device__ __forceinline__ void mdot_pass(const double* __restrict__ w, const double* __restrict__ V, long long N,
+                                          double* __restrict__ dots) {
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const double wp = w[p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = fma(wp, V[(long long)q * N + p], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double a = acc[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0 && a != 0.0) atomicAdd(dots + q, a);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ w, const double* __restrict__ V, int k,
                                              long long N, double* __restrict__ dots) {
   for (int i0 = 0; i0 < k; i0 += kMdotVec) {
-    const int nv = min(kMdotVec, k - i0);
-    double acc[kMdotVec];
-#pragma unroll
-    for (int q = 0; q < kMdotVec; ++q) acc[q] = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-      const double wp = w[p];
-#pragma unroll
-      for (int q = 0; q < kMdotVec; ++q)
-        if (q < nv) acc[q] = fma(wp, V[(long long)(i0 + q) * N + p], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < kMdotVec; ++q) {
-      if (q >= nv) break;
-      double a = acc[q];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-      if ((threadIdx.x & 31) == 0 && a != 0.0) atomicAdd(dots + i0 + q, a);
+    const double* Vi = V + (long long)i0 * N;
+    switch (min(kMdotVec, k - i0)) {
+      case 8: mdot_pass<8>(w, Vi, N, dots + i0); break;
+      case 7: mdot_pass<7>(w, Vi, N, dots + i0); break;
+      case 6: mdot_pass<6>(w, Vi, N, dots + i0); break;
+      case 5: mdot_pass<5>(w, Vi, N, dots + i0); break;
+      case 4: mdot_pass<4>(w, Vi, N, dots + i0); break;
+      case 3: mdot_pass<3>(w, Vi, N, dots + i0); break;
+      case 2: mdot_pass<2>(w, Vi, N, dots + i0); break;
+      default: mdot_pass<1>(w, Vi, N, dots + i0); break;
     }
   }
 }

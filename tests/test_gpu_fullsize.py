@@ -1,6 +1,6 @@
 """The bench workload at full size (three ellipsoids, 256^3, Dirichlet data,
-precision 2 with GMRES(30), trilinear prolongation and full-weighting
-restriction, as bench.py runs it),
+precision 2 with flexible GMRES(30) and classical Gram-Schmidt, trilinear
+prolongation and full-weighting restriction, as bench.py runs it),
 checked on sampled outputs.
 
 The oracle cannot build the 256^3 hierarchy in test time, so the solution is
@@ -53,7 +53,8 @@ def solved():
     prob = W.ellipsoids_problem(N, 0)
     prob.shape_bc = W.DIRICHLET
     S = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, precision=2, krylov=1,
-                    min_coarse_n=32, krylov_restart=30, max_iter=2000, prolong=1, restriction=1)
+                    min_coarse_n=32, krylov_restart=30, max_iter=2000, prolong=1, restriction=1,
+                    krylov_cgs=1)
     f = ccmg.cell_averages_terms(S, W.rhs_terms(prob))
     gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact, prob.box_bc)
     gp = ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, prob.shape_bc)

@@ -205,15 +205,17 @@ def test_solve_host_buffers(pair):
     assert np.abs(phi - phi_d.cpu().numpy()).max() < 1e-12 * np.abs(phi).max()
 
 
+@pytest.mark.parametrize("cgs", [0, 1])
 @pytest.mark.parametrize("flexible", [0, 1])
-def test_gmres_acceleration(pair, flexible):
+def test_gmres_acceleration(pair, flexible, cgs):
     """GMRES right-preconditioned by the same V-cycle (plain, or flexible with the
-    preconditioned vectors kept) reaches the same discrete solution (the
-    oracle's converged Alg. Multigrid) in fewer V-cycles."""
+    preconditioned vectors kept; modified or classical Gram-Schmidt) reaches the
+    same discrete solution (the oracle's converged Alg. Multigrid) in fewer
+    V-cycles."""
     from paper_2410_05865_gb300 import ccmg
     S, H, (f, gb, gp), r_or, prob = pair
     K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, krylov=1, krylov_restart=30,
-                    krylov_flexible=flexible)
+                    krylov_flexible=flexible, krylov_cgs=cgs)
     lv = H.levels[0]
     phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
     st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
@@ -239,6 +241,25 @@ def test_mixed_precision_solve(pair, krylov, precision):
     st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
     assert rc == 0 and st.rel_resid < 1e-10
     ref, hist, it = H.multigrid(r_or, eps=1e-10)
+    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
+    K.close()
+
+
+def test_bench_configuration_solve(pair):
+    """The configuration the benchmark runs (FP32 grid work and LU-correction
+    factors, flexible GMRES(30) with classical Gram-Schmidt, trilinear
+    prolongation, full-weighting restriction) reaches the oracle's converged
+    solution."""
+    from paper_2410_05865_gb300 import ccmg
+    S, H, (f, gb, gp), r_or, prob = pair
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, precision=2, krylov=1,
+                    krylov_restart=30, krylov_flexible=1, krylov_cgs=1, prolong=1, restriction=1)
+    lv = H.levels[0]
+    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    assert rc == 0 and st.converged and st.rel_resid < 1e-10
+    ref, hist, it = H.multigrid(r_or, eps=1e-10)
+    assert st.iters < it
     assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
     K.close()
 

@@ -1821,8 +1821,11 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
                      S->prm.krylov_cgs ? 3 : 2 * (j + 1) + 2);
         CK(cudaMemsetAsync(S->kdots, 0, sizeof(double) * (m + 2), S->stream));
         if (S->prm.krylov_cgs) {  // classical Gram-Schmidt on -w: two passes over the basis
-          k_mdot<<<grid, block, 0, S->stream>>>(S->kw, V, j + 1, N, S->kdots);
-          k_mupdate<<<grid, block, 0, S->stream>>>(S->kw, V, S->kdots, j + 1, N, S->kdots + j + 1);
+          // about a hundred elements per thread, so that the FP64 shuffle reductions
+          // (five adds per thread and vector) stay a few per cent of the products
+          const int rgrid = std::min(grid, S->nsm * 4);
+          k_mdot<<<rgrid, block, 0, S->stream>>>(S->kw, V, j + 1, N, S->kdots);
+          k_mupdate<<<rgrid, block, 0, S->stream>>>(S->kw, V, S->kdots, j + 1, N, S->kdots + j + 1);
         } else {
           for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt on -w
             k_dot<<<grid, block, 0, S->stream>>>(S->kw, V + (long long)i * N, N, S->kdots + i);

@@ -129,7 +129,10 @@ def _ptr(a):
 def default_params(**kw) -> cc_params:
     p = cc_params()
     lib().cc_default_params(C.byref(p))
+    names = {f for f, _ in cc_params._fields_}
     for k, v in kw.items():
+        if k not in names:  # ctypes would keep an unknown name as a plain attribute, unused
+            raise TypeError(f"unknown solver parameter {k!r}")
         setattr(p, k, v)
     return p
 

@@ -51,6 +51,13 @@ def test_invalid_arguments(ccmg):
     assert e.value.status == 1
 
 
+def test_unknown_parameter_rejected(ccmg):
+    """A misspelt parameter name is an error, not a silently unused attribute."""
+    assert ccmg.default_params(krylov_cgs=1).krylov_cgs == 1
+    with pytest.raises(TypeError):
+        ccmg.default_params(krylov_cg=1)
+
+
 def test_setup_error_message(ccmg):
     """A failed cc_setup leaves its reason for cc_last_error(NULL, ...)."""
     bad = [((0.5, 0.5, 0.5), (0.2, -0.1, 0.2))]

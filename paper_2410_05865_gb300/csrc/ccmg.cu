@@ -1403,7 +1403,8 @@ void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
 // the fastest for the V-cycle's precision.
 template <class T>
 cc_status tune_jacobi(cc_solver* S, DevLevel& L, T* a, T* b, T* c) {
-  static const int cand[][2] = {{16, 8}, {32, 4}, {8, 16}, {16, 16}, {32, 8}, {64, 2}, {64, 4}};
+  static const int cand[][2] = {{16, 8}, {32, 4}, {8, 16}, {16, 16}, {32, 8}, {64, 2},
+                                {64, 4}, {8, 8},  {4, 32}, {8, 32},  {4, 64}};
   CK(cudaMemsetAsync(a, 0, L.N * sizeof(T), S->stream));
   CK(cudaMemsetAsync(b, 0, L.N * sizeof(T), S->stream));
   cudaEvent_t e0, e1;

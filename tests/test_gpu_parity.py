@@ -288,7 +288,7 @@ def test_smo1_tiles_tuned(pair):
     """The set-up autotuner picks one of its candidate SMO-1 tiles for every
     smoothed level (the Jacobi parity above runs with that tile)."""
     S, H, _, _, _ = pair
-    cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4)}
+    cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4), (8, 8), (4, 32), (8, 32), (4, 64)}
     for m in range(len(H.levels) - 1):
         assert tuple(S.info.jacobi_block[m]) in cands
 

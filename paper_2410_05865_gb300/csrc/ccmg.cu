@@ -338,33 +338,6 @@ __global__ void k_resid1_z32_shell(const float* __restrict__ z, const double* __
   }
 }
 
-// The same on one launch over all cells (grids too small for the split, n < 8).
-__global__ void k_resid1_z32(const float* __restrict__ z, const double* __restrict__ s, double* __restrict__ out,
-                             const uint8_t* __restrict__ typ, StencilP P) {
-  const int n = P.n;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= n) return;
-  const int nn = n * n;
-  const int idx = (i * n + j) * n + k;
-  double r = 0.0;
-  if (typ[idx] == 1) {
-    double lz;
-    if (i >= 2 && i < n - 2 && j >= 2 && j < n - 2 && k >= 2 && k < n - 2) {
-      const unsigned int* b = reinterpret_cast<const unsigned int*>(z);
-      const unsigned int v[13] = {b[idx],          b[idx + nn],     b[idx - nn],    b[idx + n],    b[idx - n],
-                                  b[idx + 1],      b[idx - 1],      b[idx + 2 * nn], b[idx - 2 * nn], b[idx + 2 * n],
-                                  b[idx - 2 * n], b[idx + 2],     b[idx - 2]};
-      int emax;
-      const double acc = __ll2double_rn(fx_row(v, emax));
-      lz = emax == 255 ? __longlong_as_double(0x7FF8000000000000LL) : acc * fx_scale(P.inv12h2, emax);
-    } else {
-      lz = apply_regular<double, float>(z, i, j, k, P);
-    }
-    r = (s ? s[idx] : 0.0) - lz;
-  }
-  out[idx] = r;
-}
-
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          const uint8_t* __restrict__ typ, StencilP P, double* __restrict__ norm2) {
   const int n = P.n;
@@ -1450,14 +1423,11 @@ void resid(cc_solver* S, DevLevel& L, const double* phi, const double* s, double
 // out = s - L z for a z held in FP32 (s = nullptr: 0); with z64 (its exact FP64
 // copy) the phi2 rows too, else 0 there
 void resid_z32(cc_solver* S, DevLevel& L, const float* z, const double* z64, const double* s, double* out) {
-  if (L.n >= 8) {
+  {  // every level has n >= 8 (cc_setup and the coarsening stop there), so the interior is not empty
     const int m = L.n - 4, shell = L.n * L.n * L.n - m * m * m;
     ProfScope ps(S, P_RESID1, (s ? 21.0 : 13.0) * L.N, 2);
     k_resid1_z32_in<<<grid3(m, block3(m)), block3(m), 0, S->stream>>>(z, s, out, L.typ, L.P);
     k_resid1_z32_shell<<<grid_for(S, shell, 128), 128, 0, S->stream>>>(z, s, out, L.typ, L.P, shell);
-  } else {
-    ProfScope ps(S, P_RESID1, (s ? 21.0 : 13.0) * L.N);
-    k_resid1_z32<<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(z, s, out, L.typ, L.P);
   }
   if (z64 && L.n2 > 0) {
     ProfScope ps(S, P_RESID2, 12.0 * L.p2_nnz);

@@ -15,7 +15,7 @@ Paper passages followed
 * FV-PLG (Defs. "Triangular lattice", "PLG problem", Sec. 4.1) and the weighted
   least-squares fit of degree 4 (Sec. 2.3); the row is <Lap p>_i.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 * theta = 0.02 (at 0.1 the concave creases of overlapping ellipsoids lose so
   many cells to merging that no poised lattice exists); a common face must
   have positive fluid area; common faces

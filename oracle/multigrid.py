@@ -8,7 +8,7 @@ the permutation P of the nested-dissection ordering cancels
 (P^T (P L22 P^T)^{-1} P = L22^{-1}), so the oracle uses a library sparse LU
 (scipy SuperLU) of L22 itself.  The bottom solver is a sparse LU of L^(M).
 
-Readings (listed in DESIGN.md): ||.|| is the Euclidean norm over all unknowns;
+Readings where the paper is silent: ||.|| is the Euclidean norm over all unknowns;
 Restrict is the printed 2^-D sum over the children with phi2 children (and
 cells that are not unknowns) contributing zero; Prolong adds the parent's
 value to phi1 cells only, and only from parents that are phi1 cells of the

@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=64, help="grid of the oracle's CPU sample")
     ap.add_argument("--precision", type=int, default=2,
                     help="0 FP64 V-cycle; 1 FP32 grid work, FP64 LU-corrections; 2 FP32 grid work and "
-                         "LU-correction factors (FP64 PLG rows, bottom solve and outer residual)")
+                         "LU-correction factors (their PLG right-hand sides in double-float; FP64 bottom "
+                         "solve and outer residual)")
     ap.add_argument("--krylov", type=int, default=1, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
     ap.add_argument("--min-n", type=int, default=32, help="coarsening stops before n < min-n")
     ap.add_argument("--restart", type=int, default=30)
@@ -377,8 +378,8 @@ def run_ours(args):
                        "v_cycles": iters[-1], "omega": 0.5, "nu1": 3, "nu2": 3,
                        "precision": ["fp64",
                                      "fp32 grid work; fp64 LU-corrections, bottom solve, outer residual",
-                                     "fp32 grid work and LU-correction factors; fp64 PLG rows, bottom solve, "
-                                     "outer residual"][args.precision],
+                                     "fp32 grid work and LU-correction factors (PLG right-hand sides in "
+                                     "double-float); fp64 bottom solve, outer residual"][args.precision],
                        "outer": ["Alg. Multigrid",
                                  f"flexible GMRES({args.restart}) preconditioned by the V-cycle, "
                                  f"{['modified', 'classical'][args.cgs]} Gram-Schmidt"][args.krylov],

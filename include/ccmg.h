@@ -84,8 +84,12 @@ typedef struct {
                         restriction, prolongation) with FP64 LU-corrections, bottom
                         solve and outer residual (defect correction); 2: as 1, and
                         the LU-corrections of the finer levels store and apply their
-                        factors in FP32 (their right-hand sides, built from the PLG
-                        rows, the bottom solve and the outer residual stay FP64) (0) */
+                        factors in FP32, their right-hand sides (from the PLG rows
+                        and the FP32 grid values) summed in double-float FP32
+                        arithmetic, about 2^-48 of the terms (the bottom solve and
+                        the outer residual stay FP64).  With 1 and 2, GMRES applies
+                        the operator to the FP32 V-cycle output with exact
+                        fixed-point interior rows (cc_residual_f32) (0) */
   int lu_schedule;   /* triangular sweeps of the LU-corrections and bottom solve:
                         0 one launch per tree height and sweep; 1 one cooperative
                         launch per solve with bounded grid barriers between heights

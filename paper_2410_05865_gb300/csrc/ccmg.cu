@@ -489,8 +489,8 @@ __global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi,
 constexpr int kBarGroups = 16;  // group counters of the one-launch sweeps' grid barrier (after one top counter)
 
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
-// The PLG rows are applied in FP64 whatever the grid type; b is stored in the
-// LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
+// The PLG rows are applied in FP64 (k_lu_rhs_df below serves the FP32 grids
+// whose factors are FP32 too); b is stored in the LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
 template <class T, class TW>
 __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                          const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
@@ -1313,7 +1313,7 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
   const bool one = D.coop_grid > 0 && !D.coop_failed;
   {
     ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 2.0 * sizeof(TV) * D.np);
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4 && sizeof(TV) == 4)  // FP32 grid and FP32 factors: no FP64 arithmetic
       k_lu_rhs_df<TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(b, x, D.np, D.cell, D.rptr, D.rcol,
                                                                          D.rval2, s, phi, one ? D.bar : nullptr);
     else

@@ -25,17 +25,22 @@ Readings where the paper is silent:
   cell still below theta.  Cells are treated as single-component.
 * phi1 needs every in-box cell of {i, i±e^d, i±2e^d} to be a full cell that
   takes part in no merge.
-* The PLG back-tracking of [PLG] is not in the paper; the lattice is the first
-  feasible one in a fixed preference order: stage 1 (eight per-axis
-  orderings, q at the lattice corner), stage 2 (q anywhere in a lattice inside
-  a 5^3 window: zig-zag orderings from every start).  A cell without a
-  degree-4 lattice is merged into a neighbour (up to 4 rounds).  On coarse
-  levels only, degrees 3 and 2 are then tried, and cells still without a
-  lattice are dropped from the coarse problem.
-* WLS weights 1 / (1 + |c_k - c_i|^2 / h^2) with c the centroids; one boundary
-  row per lattice cell that carries a boundary patch.  A fit whose own-cell
-  coefficient is not negative is rejected like a rank-deficient one (slivers
-  next to Neumann boundaries otherwise give wrong-signed rows).
+* The PLG back-tracking of [PLG] is not in the paper.  Feasible lattices are
+  visited in a fixed preference order: stage 1 (eight per-axis orderings, q at
+  the lattice corner), stage 2 (q anywhere in a lattice inside a 5^3 window:
+  zig-zag orderings from every start).  The first whose fitted row has
+  rho = sum_{j != q} |c_j| / |c_q| <= 8 wins; if none of the first 64
+  rank-sufficient fits does, the one with the smallest rho (rows with a large
+  rho gave the operator spurious low-energy modes on a few cells).  A cell
+  without a degree-4 lattice is merged into a neighbour (up to 4 rounds).  On
+  coarse levels only, degrees 3 and 2 are then tried, and cells still without
+  a lattice are dropped from the coarse problem.
+* WLS weights 1 / (1 + |c_k - c_i|^2 / h^2)^2 with c the centroids; one boundary
+  row per lattice cell that carries a boundary patch, and one per box face of a
+  plain full lattice cell that lies on the box (the walls are boundary too, so
+  a phi2 row next to the box sees the wall data as the ghost-eliminated regular
+  rows do).  A fit whose own-cell coefficient is not negative is rejected like
+  a rank-deficient one.
 """
 from __future__ import annotations
 
@@ -51,6 +56,15 @@ from .geometry import GL_W, GL_X, MONO, MONO3, MONO_INDEX, Q, CellGeometry
 THETA = 0.02
 AREA_TIE = 1e-12   # common-face areas (units h^2) this close count as equal
 RANK_TOL = 1e-10   # min |R_kk| / max |R_kk| of the weighted LS matrix
+RHO_MAX = 8.0      # a fitted row with sum_{j != q} |c_j| <= RHO_MAX |c_q| is accepted at once
+CAND_MAX = 64      # otherwise the best of this many rank-sufficient fits
+
+
+def wls_weight(d2):
+    """WLS weight of a row whose centroid lies sqrt(d2) cell widths from the fitted
+    cell's centroid: 1 / (1 + d2)^2 (the paper only says that the weights depend
+    on the relative position)."""
+    return 1.0 / (1.0 + d2) ** 2
 
 DIRICHLET = 0
 NEUMANN = 1
@@ -485,28 +499,46 @@ class Level:
                                                 s[MONO_INDEX[(0, 0, 1)]]]) / s[0]
 
     def plg_row(self, q, degrees=(4,)):
-        """First feasible triangular lattice (Def. PLG problem) and its WLS row, or None.
+        """Triangular lattice (Def. PLG problem) and its WLS row, or None.
 
-        Degrees in ``degrees`` are tried in turn; for each, stage 1 then stage 2."""
+        Degrees in ``degrees`` are tried in turn; for each, the feasible lattices
+        are visited in preference order (stage 1, then stage 2).  A lattice whose
+        fitted row has rho = sum_{j != q} |c_j| / |c_q| <= RHO_MAX wins at once;
+        otherwise, after CAND_MAX rank-sufficient fits (or the last lattice), the
+        fit with the smallest rho is taken."""
         cq = self.coords(q)
         feas = self._slotpad[cq[0]:cq[0] + 9, cq[1]:cq[1] + 9, cq[2]:cq[2] + 9]
         for degree in degrees:
             stages, lattice = PLG_TABLES[degree]
+            best, best_rho, fits = None, np.inf, 0
             for ords, triples, offs in stages:
+                if fits >= CAND_MAX:
+                    break
                 ok = np.all(feas[offs[:, :, 0] + 4, offs[:, :, 1] + 4, offs[:, :, 2] + 4], axis=1)
                 for t in np.nonzero(ok)[0]:
                     cells = [self.index(cq + o) for o in offs[t]]
                     row = self.wls_row(q, cells, degree)
                     if row is None:
                         continue
-                    self.plg[q] = (degree, triples[t], cells)
-                    return row
+                    ent = row[0]
+                    rho = sum(abs(v) for j, v in ent.items() if j != q) / abs(ent[q])
+                    if rho <= RHO_MAX:
+                        self.plg[q] = (degree, triples[t], cells)
+                        return row
+                    if rho < best_rho:
+                        best, best_rho = (row, (degree, triples[t], cells)), rho
+                    fits += 1
+                    if fits >= CAND_MAX:
+                        break
+            if best is not None:
+                self.plg[q] = best[1]
+                return best[0]
         return None
 
     def wls_row(self, q, cells, degree=4):
         """Weighted LS fit in Pi_degree^3 over the lattice cells (+ boundary patches).
 
-        Returns ({cell: coef}, [(('patch', owner), coef)]) for <Lap p>_q, or None
+        Returns ({cell: coef}, [(('patch', owner) | ('box', face id), coef)]) for <Lap p>_q, or None
         if the weighted LS matrix is numerically rank deficient.
         """
         h = self.h
@@ -516,7 +548,7 @@ class Level:
         for j in cells:
             m = shift_moments(self.vol_moments(j), self.coords(j) - cq, MONO)
             A.append(m / m[0])
-            wts.append(1.0 / (1.0 + np.sum((self.centroid(j) - cen_q) ** 2)))
+            wts.append(wls_weight(np.sum((self.centroid(j) - cen_q) ** 2)))
         for j in cells:
             if self.patch_area(j) <= 0.0:
                 continue
@@ -536,8 +568,24 @@ class Level:
                             row[k] += e[d] * sn[d][MONO3.index(tuple(lower))]
                 row /= area
             A.append(row)
-            wts.append(1.0 / (1.0 + np.sum((self.patch_centroid(j) - cen_q) ** 2)))
-            bnd.append(j)
+            wts.append(wls_weight(np.sum((self.patch_centroid(j) - cen_q) ** 2)))
+            bnd.append(("patch", j))
+        # the box walls are boundary too: a plain full lattice cell on a wall
+        # contributes the wall's condition on its face
+        n = self.n
+        for j in cells:
+            if self.kind[j] != 1 or self.merged[j]:
+                continue
+            cj = self.coords(j)
+            for d in range(3):
+                for side in (0, 1):
+                    if cj[d] != (n - 1 if side else 0):
+                        continue
+                    A.append(self._box_face_row(cj - cq, d, side))
+                    fc = cj + 0.5
+                    fc[d] = cj[d] + side
+                    wts.append(wls_weight(np.sum((fc - cen_q) ** 2)))
+                    bnd.append(("box", self.face_id(d, side, cj), self.box_bc[2 * d + side]))
         nb = len(_monos(degree))
         A = np.array(A)[:, :nb]
         sw = np.sqrt(np.array(wts))
@@ -564,9 +612,39 @@ class Level:
         if not ent.get(q, 0.0) < 0.0:
             return None  # a Laplacian row needs a negative diagonal: reject this fit
         g = []
-        for j, b in zip(bnd, beta[nc:]):
-            g.append((("patch", j), b * (h if self.shape_bc == NEUMANN else 1.0)))
+        for key, b in zip(bnd, beta[nc:]):
+            if key[0] == "patch":
+                g.append((key, b * (h if self.shape_bc == NEUMANN else 1.0)))
+            else:
+                g.append((key[:2], b * (h if key[2] == NEUMANN else 1.0)))
         return ent, g
+
+    def _box_face_row(self, delta, d, side):
+        """Average over a box face of the lattice cell at offset ``delta`` from q of
+        xi^alpha (Dirichlet wall) or of d xi^alpha / d n, n outward (Neumann wall),
+        xi about q's centre in units of h; 3-point Gauss-Legendre per tangential
+        axis (exact: degree <= 4 in each)."""
+        x3, w3 = np.polynomial.legendre.leggauss(3)
+        t = [a for a in range(3) if a != d]
+        xn = delta[d] + (0.5 if side else -0.5)
+        sgn = 1.0 if side else -1.0
+        neumann = self.box_bc[2 * d + side] == NEUMANN
+        row = np.zeros(35)
+        for a, wa in zip(x3, w3):
+            for b, wb in zip(x3, w3):
+                xi = np.zeros(3)
+                xi[d] = xn
+                xi[t[0]] = delta[t[0]] + 0.5 * a
+                xi[t[1]] = delta[t[1]] + 0.5 * b
+                w = 0.25 * wa * wb
+                for k, e in enumerate(MONO):
+                    if not neumann:
+                        row[k] += w * xi[0] ** e[0] * xi[1] ** e[1] * xi[2] ** e[2]
+                    elif e[d] >= 1:
+                        ee = list(e)
+                        ee[d] -= 1
+                        row[k] += w * sgn * e[d] * xi[0] ** ee[0] * xi[1] ** ee[1] * xi[2] ** ee[2]
+        return row
 
     # ------------------------------------------------------------- data
     def box_face_averages(self, fn_dirichlet, fn_neumann_grad):

@@ -10,10 +10,13 @@ the permutation P of the nested-dissection ordering cancels
 
 Readings where the paper is silent: ||.|| is the Euclidean norm over all unknowns;
 Restrict is the printed 2^-D sum over the children with phi2 children (and
-cells that are not unknowns) contributing zero; Prolong adds the parent's
-value to phi1 cells only, and only from parents that are phi1 cells of the
-coarse level; a V-cycle starts from a zero correction on every
-level (Sec. 6.3 uses a zero initial guess).
+cells that are not unknowns) contributing zero; the correction is prolongated
+to phi1 cells only (fine phi2 cells are set by the LU-correction that
+follows), from every coarse unknown, by cell-centred trilinear interpolation
+(default; the printed patch-wise constant Prolong is kept as an option: with
+it the V-cycle factor grows with the number of levels even in the box without
+any shape); a V-cycle starts from a zero correction on every level (Sec. 6.3
+uses a zero initial guess).
 """
 from __future__ import annotations
 
@@ -91,29 +94,81 @@ def restrict(fine_ops, coarse_ops, pmap, t):
     return out
 
 
-def prolong(fine_ops, coarse_ops, pmap, e_coarse, phi, from_coarse_phi2=False):
-    """Prolong: phi1 += the parent's value (patch-wise constant).
+def prolong(fine_ops, coarse_ops, pmap, e_coarse, phi, into_phi2=False):
+    """Prolong (patch-wise constant): phi1 += the parent's value.
 
-    Reading of "leaving the correction ... for cells in phi2 to zero": the
-    correction of a coarse phi2 cell is not prolongated, and fine phi2 cells
-    receive none (the LU-correction that follows sets them).  Alg. FMG
-    prolongates a whole solution, from every coarse unknown
-    (from_coarse_phi2=True)."""
+    Reading of "leaving the correction ... for cells in phi2 to zero": fine phi2
+    cells receive no correction (the LU-correction that follows sets them);
+    every coarse unknown, phi1 or phi2, passes its value on.  Alg. FMG
+    prolongates a whole solution, into every fine unknown (into_phi2=True)."""
     out = phi.copy()
-    ec = np.zeros_like(e_coarse)
-    keep = slice(None) if from_coarse_phi2 else coarse_ops.i1
-    ec[keep] = e_coarse[keep]
-    p = pmap[fine_ops.i1]
-    out[fine_ops.i1] += np.where(p >= 0, ec[np.maximum(p, 0)], 0.0)
+    tgt = slice(None) if into_phi2 else fine_ops.i1
+    p = pmap[tgt]
+    out[tgt] += np.where(p >= 0, e_coarse[np.maximum(p, 0)], 0.0)
+    return out
+
+
+def trilinear_matrix(fine, coarse):
+    """Cell-centred trilinear interpolation from level m+1 to level m (sparse, fine x coarse).
+
+    Fine cell i lies at i/2 - 1/4 in coarse index units, so per axis it takes
+    3/4 of coarse cell floor(i/2) and 1/4 of its neighbour on i's side
+    (floor(i/2) - 1 for even i, + 1 for odd i); the 3-D weights are the
+    products.  Of the 8 coarse cells only those inside the box that are coarse
+    unknowns in their own slot (phi1 or phi2; not exterior, not absorbed by a
+    merge) count, and the kept weights are divided by their sum, so constants
+    are reproduced.  Transfer orders 2 (this) + 1 (Restrict) exceed the order
+    2 of the Laplacian, which piecewise-constant prolongation (order 1) does not."""
+    nc = coarse.n
+    rows, cols, vals = [], [], []
+    for r, o in enumerate(fine.slots):
+        c = fine.coords(int(o))
+        base = c // 2
+        side = np.where(c % 2 == 0, -1, 1)
+        ent = []
+        for sx in (0, 1):
+            for sy in (0, 1):
+                for sz in (0, 1):
+                    q = base + np.array([sx, sy, sz]) * side
+                    if np.any(q < 0) or np.any(q >= nc):
+                        continue
+                    u = coarse.uid[coarse.index(q)]
+                    if u < 0:
+                        continue
+                    w = (0.25 if sx else 0.75) * (0.25 if sy else 0.75) * (0.25 if sz else 0.75)
+                    ent.append((int(u), w))
+        tot = sum(w for _, w in ent)
+        for u, w in ent:
+            rows.append(r)
+            cols.append(u)
+            vals.append(w / tot)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(fine.slots), len(coarse.slots)))
+
+
+def prolong_trilinear(fine_ops, P, e_coarse, phi, into_phi2=False):
+    """Prolong by trilinear interpolation (``P`` from trilinear_matrix); phi1 cells
+    receive it (every fine unknown with into_phi2=True)."""
+    out = phi.copy()
+    add = P @ e_coarse
+    tgt = slice(None) if into_phi2 else fine_ops.i1
+    out[tgt] += add[tgt]
     return out
 
 
 class Hierarchy:
-    def __init__(self, levels, omega=0.5, nu1=3, nu2=3):
+    """The level hierarchy with Alg. VCycle / Alg. Multigrid / Alg. FMG.
+
+    prolongation: "trilinear" (default; see trilinear_matrix) or "constant"
+    (the printed patch-wise constant Prolong)."""
+
+    def __init__(self, levels, omega=0.5, nu1=3, nu2=3, prolongation="trilinear"):
         self.levels = levels
         self.ops = [LevelOps(lv) for lv in levels]
         self.pmaps = [parent_map(levels[m], levels[m + 1]) for m in range(len(levels) - 1)]
         self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        self.prolongation = prolongation
+        self.P = ([trilinear_matrix(levels[m], levels[m + 1]) for m in range(len(levels) - 1)]
+                  if prolongation == "trilinear" else None)
 
     @property
     def M(self):
@@ -121,6 +176,11 @@ class Hierarchy:
 
     def bottom(self, s):
         return self.ops[self.M].full_lu().solve(s)
+
+    def prolong(self, m, ec, phi, into_phi2=False):
+        if self.prolongation == "trilinear":
+            return prolong_trilinear(self.ops[m], self.P[m], ec, phi, into_phi2)
+        return prolong(self.ops[m], self.ops[m + 1], self.pmaps[m], ec, phi, into_phi2)
 
     def vcycle(self, m, s):
         """Alg. VCycle on level m for L^(m) phi = s, from a zero start."""
@@ -132,7 +192,7 @@ class Hierarchy:
         t = residual(ops, phi, s)
         sc = restrict(ops, self.ops[m + 1], self.pmaps[m], t)
         ec = self.vcycle(m + 1, sc)
-        phi = prolong(ops, self.ops[m + 1], self.pmaps[m], ec, phi)
+        phi = self.prolong(m, ec, phi)
         phi = smooth(ops, phi, s, self.omega, self.nu2)
         return phi
 
@@ -159,8 +219,7 @@ class Hierarchy:
             rs.append(restrict(self.ops[m], self.ops[m + 1], self.pmaps[m], rs[-1]))
         phi = self.bottom(rs[self.M])
         for m in range(self.M - 1, -1, -1):
-            phi = prolong(self.ops[m], self.ops[m + 1], self.pmaps[m], phi, np.zeros(len(rs[m])),
-                          from_coarse_phi2=True)
+            phi = self.prolong(m, phi, np.zeros(len(rs[m])), into_phi2=True)
             for _ in range(n_vcycles):
                 phi = phi + self.vcycle(m, rs[m] - self.ops[m].L @ phi)
         return phi

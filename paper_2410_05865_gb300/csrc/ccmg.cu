@@ -440,7 +440,7 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
   const int idx = (i * n + j) * n + k;
   if (typ[idx] != 1) return;
   const int I = ((i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
-  if (typ_c[I] == 1) phi[idx] += coarse[I];
+  if (typ_c[I] != 0) phi[idx] += coarse[I];
 }
 
 // Trilinear (cell-centred) prolongation, an option beside the paper's piecewise-
@@ -473,7 +473,7 @@ __global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi,
         const int kk = K + c * dk;
         if (kk < 0 || kk >= nc) continue;
         const int q = (ii * nc + jj) * nc + kk;
-        if (typ_c[q] != 1) continue;
+        if (typ_c[q] == 0) continue;
         const T w = wa * wb * (c ? T(0.25) : T(0.75));
         acc += w * coarse[q];
         wsum += w;
@@ -825,13 +825,18 @@ __global__ void k_merge_f(int ng, const int* __restrict__ owner, const int* __re
   }
 }
 
-// phi2 rows: r -= sum_b coef_b <<g>>_b
+// phi2 rows: r -= sum_b coef_b g_b, g_b a patch average <<g>> (code >= 0) or a
+// box face average <g> (code -(1 + face id))
 __global__ void k_patch_terms(int n2, const int* __restrict__ cell, const int* __restrict__ bptr,
                               const int* __restrict__ bpatch, const double* __restrict__ bcoef,
-                              const double* __restrict__ gpatch, double* __restrict__ r) {
+                              const double* __restrict__ gpatch, const double* __restrict__ gbox,
+                              double* __restrict__ r) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += gridDim.x * blockDim.x) {
     double v = 0.0;
-    for (int p = bptr[q]; p < bptr[q + 1]; ++p) v += bcoef[p] * gpatch[bpatch[p]];
+    for (int p = bptr[q]; p < bptr[q + 1]; ++p) {
+      const int b = bpatch[p];
+      v += bcoef[p] * (b >= 0 ? gpatch[b] : gbox[-1 - b]);
+    }
     r[cell[q]] -= v;
   }
 }
@@ -1600,7 +1605,7 @@ cc_status build_rhs(cc_solver* S, const double* f, const double* gbox, const dou
                                                                     S->g_w, S->f, S->r);
   if (S->n2_0)
     k_patch_terms<<<grid_for(S, S->n2_0, 128), 128, 0, S->stream>>>(S->n2_0, L.p2_cell, S->b_ptr, S->b_patch,
-                                                                     S->b_coef, S->gpatch, S->r);
+                                                                     S->b_coef, S->gpatch, S->gbox, S->r);
   CK(cudaGetLastError());
   return CC_OK;
 }
@@ -1935,7 +1940,7 @@ void cc_default_params(cc_params* p) {
   p->precision = 0;
   p->lu_schedule = 0;
   p->krylov_cgs = 0;
-  p->prolong = 0;
+  p->prolong = 1;
   p->restriction = 0;
   p->krylov_flexible = 1;
 }
@@ -2171,7 +2176,9 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     std::vector<int> patch_of = finish_host_info(S);
     TRY(dalloc(S, &S->gpatch, S->patch_owner.size()));
     std::vector<int> bp(L0.p2_bpatch.size());
-    for (size_t q = 0; q < bp.size(); ++q) bp[q] = patch_of[L0.p2_bpatch[q]];
+    // patch terms index g_patch; box-face terms keep their code -(1 + face id) into g_box
+    for (size_t q = 0; q < bp.size(); ++q)
+      bp[q] = L0.p2_bpatch[q] < 0 ? L0.p2_bpatch[q] : patch_of[L0.p2_bpatch[q]];
     S->n2_0 = D0.n2;
     TRY(dupload(S, &S->b_ptr, L0.p2_bptr));
     TRY(dupload(S, &S->b_patch, bp));
@@ -2336,7 +2343,7 @@ cc_status cc_phi2_rows(const cc_solver* S, int level, int32_t* cells, int32_t* p
     if (vals) vals[q] = L.p2_val[q];
   }
   for (size_t q = 0; q < L.p2_bpatch.size(); ++q) {
-    if (bpatch) bpatch[q] = level == 0 ? pnum[L.p2_bpatch[q]] : L.p2_bpatch[q];
+    if (bpatch) bpatch[q] = (level == 0 && L.p2_bpatch[q] >= 0) ? pnum[L.p2_bpatch[q]] : L.p2_bpatch[q];
     if (bcoef) bcoef[q] = L.p2_bcoef[q];
   }
   return CC_OK;

@@ -4,17 +4,21 @@
 //    |C| < theta h^3 into the theta-proper face neighbour with the largest
 //    common (fluid) face (faces within 1e-12 h^2 of the largest tie), ties to
 //    the lowest index; any cell still below theta
-//    grows by breadth-first search.  theta = 0.1.
+//    grows by breadth-first search.  theta = 0.02.
 //  * The phi1/phi2 split (Sec. 2.3-2.4): phi1 iff every in-box cell of
 //    {i, i±e^d, i±2e^d} is a full cell taking part in no merge.
 //  * eq. regularLaplaceDiscretization with the box ghosts of Sec. 2.3 eliminated
 //    (second Dirichlet ghost coefficient of <g> read as 300).
-//  * FV-PLG (Sec. 4.1): the first triangular lattice T_4^3 of feasible cells in a
-//    fixed preference order of per-axis coordinate orderings; on coarse levels a
-//    cell without one falls back to degree 3, then 2.
+//  * FV-PLG (Sec. 4.1): triangular lattices T_4^3 of feasible cells in a fixed
+//    preference order of per-axis coordinate orderings; the first whose fitted
+//    row has rho = sum_{j != q} |c_j| / |c_q| <= 8 wins, else the smallest rho
+//    among the first 64 fits; on coarse levels a cell without one falls back to
+//    degree 3, then 2.
 //  * The weighted least-squares fit in Pi_p^3 (Sec. 2.3): rows are cell averages
-//    of the lattice cells and one boundary row per lattice cell with a patch;
-//    weights 1/(1 + |c_k - c_i|^2/h^2) (centroids); the phi2 row is <Lap p>_i.
+//    of the lattice cells, one boundary row per lattice cell with a patch, and
+//    one per box face of a plain full lattice cell on the box (the box is part
+//    of the boundary); weights 1/(1 + |c_k - c_i|^2/h^2)^2 (centroids); the
+//    phi2 row is <Lap p>_i.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -28,6 +32,22 @@
 namespace ccmg {
 
 namespace {
+
+// Weight of a WLS row whose centroid lies d2 (squared, units of h^2) from the
+// fitted cell's centroid: 1 / (1 + d2)^2.  The squared form ties the fit to the
+// nearest cells; with 1 / (1 + d2) the rows of small cut cells came out with
+// off-diagonal sums up to thousands of times their diagonal, and the operator
+// had spurious low-energy modes on a few cells.
+double wls_weight(double d2) {
+  const double w = 1.0 / (1.0 + d2);
+  return w * w;
+}
+
+// Lattice choice by row quality: rho = sum_{j != q} |c_j| / |c_q| of the fitted
+// row.  The first lattice (in preference order) with rho <= kRhoMax wins;
+// otherwise the smallest rho among the first kCandMax rank-sufficient fits.
+constexpr double kRhoMax = 8.0;
+constexpr int kCandMax = 64;
 
 // ----------------------------------------------------------- shift tables
 // (T m)[alpha] = sum_{beta<=alpha} prod_d C(alpha_d,beta_d) delta_d^(alpha_d-beta_d) m[beta]
@@ -513,7 +533,7 @@ struct LevelBuilder {
       centroid(j, c);
       double d2 = 0;
       for (int t = 0; t < 3; ++t) d2 += (c[t] - cenq[t]) * (c[t] - cenq[t]);
-      wts.push_back(1.0 / (1.0 + d2));
+      wts.push_back(wls_weight(d2));
     }
     for (int j : cells) {
       if (patch_area(j) <= 0.0) continue;
@@ -547,8 +567,67 @@ struct LevelBuilder {
       patch_centroid(j, c);
       double d2 = 0;
       for (int t = 0; t < 3; ++t) d2 += (c[t] - cenq[t]) * (c[t] - cenq[t]);
-      wts.push_back(1.0 / (1.0 + d2));
+      wts.push_back(wls_weight(d2));
       bnd.push_back(j);
+    }
+    // Box faces are part of the boundary too: a plain full lattice cell on a
+    // wall adds that wall's condition on its face (Dirichlet: the face average
+    // of xi^alpha; Neumann: of d xi^alpha / d n, n outward), so that a phi2
+    // row next to the box sees the box data just as the ghost-eliminated
+    // regular rows do.  Encoded in bnd as -(1 + box face id).
+    for (int j : cells) {
+      if (L.geo.kind[j] != 1 || L.merged[j]) continue;
+      int cj[3];
+      coords(j, cj);
+      for (int dn = 0; dn < 3; ++dn)
+        for (int side = 0; side < 2; ++side) {
+          if (cj[dn] != (side ? n - 1 : 0)) continue;
+          // 1-D averages of xi^k over the face: normal coordinate fixed, the
+          // tangential ones over [c - 1/2, c + 1/2] relative to q's centre
+          double avg[3][5];
+          for (int t = 0; t < 3; ++t) {
+            const double c = cj[t] - cq[t];
+            if (t == dn) {
+              const double x = c + (side ? 0.5 : -0.5);
+              avg[t][0] = 1.0;
+              for (int k = 1; k < 5; ++k) avg[t][k] = avg[t][k - 1] * x;
+            } else {
+              const double a = c - 0.5, b = c + 0.5;
+              double qa = a, qb = b;  // a^(k+1), b^(k+1)
+              for (int k = 0; k < 5; ++k) {
+                avg[t][k] = (qb - qa) / (k + 1);
+                qa *= a;
+                qb *= b;
+              }
+            }
+          }
+          const int bc = L.box_bc[2 * dn + side];
+          const double nrm = side ? 1.0 : -1.0;
+          double row[kNMono];
+          for (int k = 0; k < kNMono; ++k) {
+            const int e[3] = {M.e[k][0], M.e[k][1], M.e[k][2]};
+            if (bc == BC_DIRICHLET) {
+              row[k] = avg[0][e[0]] * avg[1][e[1]] * avg[2][e[2]];
+            } else {
+              double s = 0.0;
+              if (e[dn] >= 1) {
+                int f[3] = {e[0], e[1], e[2]};
+                f[dn] -= 1;
+                s = nrm * e[dn] * avg[0][f[0]] * avg[1][f[1]] * avg[2][f[2]];
+              }
+              row[k] = s;
+            }
+          }
+          for (int t = 0; t < nb; ++t) A.push_back(row[t]);
+          double c[3] = {cj[0] + 0.5, cj[1] + 0.5, cj[2] + 0.5};
+          c[dn] = cj[dn] + (side ? 1.0 : 0.0);
+          double d2 = 0;
+          for (int t = 0; t < 3; ++t) d2 += (c[t] - cenq[t]) * (c[t] - cenq[t]);
+          wts.push_back(wls_weight(d2));
+          const int t0 = dn == 0 ? cj[1] : cj[0];
+          const int t1 = dn == 2 ? cj[1] : cj[2];
+          bnd.push_back(-1 - ((2 * dn + side) * n + t0) * n - t1);
+        }
     }
     const int m = (int)wts.size();
     std::vector<double> sw(m);
@@ -610,7 +689,9 @@ struct LevelBuilder {
     for (size_t b = 0; b < bnd.size(); ++b) {
       int i = nc + (int)b;
       double coef = sw[i] * y[i] * inv_h2;
-      if (L.shape_bc == BC_NEUMANN) coef *= h;
+      const int fid = bnd[b] < 0 ? -1 - bnd[b] : -1;
+      const int bc = fid < 0 ? L.shape_bc : L.box_bc[fid / (n * n)];
+      if (bc == BC_NEUMANN) coef *= h;
       out.bpatch.push_back(bnd[b]);
       out.bcoef.push_back(coef);
     }
@@ -641,7 +722,10 @@ struct LevelBuilder {
     std::vector<int> cells;
     for (int di = 0; di < ndeg; ++di) {
       const PlgTable& T = plg_table(degrees[di]);
-      for (int stage = 0; stage < 2; ++stage) {
+      RowOut best;
+      double best_rho = 1e300;
+      int tried = 0;
+      for (int stage = 0; stage < 2 && tried < kCandMax; ++stage) {
         const auto& ords = stage == 0 ? T.ords : T.ords2;
         const auto& triples = stage == 0 ? T.triples : T.triples2;
         for (const auto& t : triples) {
@@ -660,8 +744,23 @@ struct LevelBuilder {
             int p[3] = {cq[0] + ox[k[0]], cq[1] + oy[k[1]], cq[2] + oz[k[2]]};
             cells.push_back(index(p));
           }
-          if (wls_row(q, cells, degrees[di], out)) return true;
+          if (!wls_row(q, cells, degrees[di], out)) continue;
+          double dg = 0.0, off = 0.0;
+          for (size_t i = 0; i < out.cols.size(); ++i)
+            if (out.cols[i] == q) dg += out.vals[i];
+            else off += std::fabs(out.vals[i]);
+          const double rho = off / std::fabs(dg);
+          if (rho <= kRhoMax) return true;
+          if (rho < best_rho) {
+            best_rho = rho;
+            best = out;
+          }
+          if (++tried >= kCandMax) break;
         }
+      }
+      if (best.ok) {
+        out = best;
+        return true;
       }
     }
     return false;

@@ -1,20 +1,30 @@
-"""GPU path against the oracle, step by step, through the C ABI (sphere configuration).
+"""GPU path against the oracle, step by step, through the C ABI.
 
-Inputs are seeded and synthetic: the sphere problem of radius 0.25 at 32^3
-(levels 32 and 16).  Every hot-path step (Sec. 5.3: residual, SMO-1, SMO-2,
-Restrict, Prolong, bottom solve, Alg. VCycle, Alg. Multigrid) is run by the
-CUDA library on device buffers and compared element by element with the
-oracle on the same inputs.
+Inputs are seeded and synthetic, on two hierarchies at 32^3 with coarsening
+down to 8^3 (levels 32, 16, 8):
+* the sphere configuration (radius 0.25, Dirichlet everywhere);
+* the three-ellipsoid configuration of seed 0 with Neumann data on the
+  ellipsoids, whose levels carry merged cells, rows of lower degree on the
+  coarsest level, phi2 rows next to the box (box-face terms) and Neumann
+  patch rows.
+Every hot-path step (Sec. 5.3: residual, SMO-1, SMO-2, Restrict, Prolong,
+bottom solve, Alg. VCycle, Alg. Multigrid) is run by the CUDA library on device
+buffers, on every level, and compared element by element with the oracle on
+the same inputs.
 
 Tolerances (FP64):
 * steps that are sums of at most ~50 products (residual, Jacobi, transfers,
   RHS assembly): 1e-12 relative to the largest term magnitude;
 * steps that solve with an LU factor (SMO-2, bottom solve, V-cycle): the GPU
-  uses its own nested-dissection LU without pivoting, the oracle SuperLU with
-  partial pivoting, so they agree to cond(A) * eps; 1e-10 relative;
+  uses its own nested-dissection LU with pivoting inside supernodes, the
+  oracle SuperLU, so they agree to cond(A) * eps; 1e-10 relative;
+* trajectories (k V-cycles from the same start): 1e-10 relative per step;
 * the whole solve: both stop below 1e-10 relative residual; the solutions
   then agree to 1e-10 / (1 - factor) times cond(L), taken as 1e-7 relative,
   and the error against the exact cell averages matches.
+FP32 V-cycle (precision 2: FP32 grid kernels, FP32 factors, double-float LU
+right-hand sides) against the FP64 oracle V-cycle: 2e-5 relative (FP32 rounding
+of about 50 operations per cell and level, times the LU solves' growth).
 """
 import numpy as np
 import pytest
@@ -28,28 +38,40 @@ from oracle import multigrid as MG
 pytestmark = pytest.mark.gpu
 
 N = 32
+MIN_N = 8
+CONFIGS = ["sphere", "ellipsoids_neumann"]
 
 
-@pytest.fixture(scope="module")
-def pair():
+def problem(name):
+    return W.sphere_problem(N) if name == "sphere" else W.ellipsoids_problem(N, 0)
+
+
+@pytest.fixture(scope="module", params=CONFIGS)
+def pair(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2410_05865_gb300 import ccmg
-    prob = W.sphere_problem(N)
-    S = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0)
-    levels = D.build_hierarchy(N, prob.shapes, prob.shape_bc, prob.box_bc)
+    prob = problem(request.param)
+    S = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N)
+    levels = D.build_hierarchy(N, prob.shapes, prob.shape_bc, prob.box_bc, min_n=MIN_N)
     H = MG.Hierarchy(levels)
-    assert S.levels == [lv.n for lv in levels]
+    assert S.levels == [lv.n for lv in levels] == [32, 16, 8]
     # data for each side from its own quadrature
     f = ccmg.cell_averages(S, W.lap_phi_exact)
-    gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact)
+    gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact, prob.box_bc)
     gp = ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, prob.shape_bc)
     lv = levels[0]
     fo = lv.cell_averages(W.lap_phi_exact)
     gbo = lv.box_face_averages(W.phi_exact, W.grad_phi_exact)
     gpo = lv.patch_averages(W.phi_exact, W.grad_phi_exact)
     r_or = lv.rhs(fo, gbo, gpo)
-    return S, H, (f, gb, gp), r_or, prob
+    yield S, H, (f, gb, gp), r_or, prob
+    S.close()
+
+
+def solver(prob, **kw):
+    from paper_2410_05865_gb300 import ccmg
+    return ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N, **kw)
 
 
 def dev(x):
@@ -90,7 +112,7 @@ def test_rhs_parity(pair):
     assert rel(from_grid(lv, r), r_or, np.abs(r_or).max()) < 1e-12
 
 
-@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("level", [0, 1, 2])
 def test_residual_parity(pair, level):
     S, H, _, _, _ = pair
     lv, ops = H.levels[level], H.ops[level]
@@ -117,13 +139,14 @@ def test_jacobi_parity(pair, level):
     assert rel(from_grid(lv, out.cpu()), ref, np.abs(ref).max()) < 1e-12
 
 
-def test_lu_correction_parity(pair):
+@pytest.mark.parametrize("level", [0, 1])
+def test_lu_correction_parity(pair, level):
     S, H, _, _, _ = pair
-    lv, ops = H.levels[0], H.ops[0]
+    lv, ops = H.levels[level], H.ops[level]
     phi = rand_unknowns(lv, 5)
     s = rand_unknowns(lv, 6) * 1e3
     g = dev(to_grid(lv, phi))
-    S.lu_correction(0, g, dev(to_grid(lv, s)))
+    S.lu_correction(level, g, dev(to_grid(lv, s)))
     S.sync()
     ref = MG.lu_correction(ops, phi, s)
     got = from_grid(lv, g.cpu())
@@ -133,23 +156,40 @@ def test_lu_correction_parity(pair):
     assert np.abs(res[ops.i2]).max() < 1e-9 * np.abs(s).max()
 
 
-def test_transfer_parity(pair):
+@pytest.mark.parametrize("level", [0, 1])
+def test_restrict_parity(pair, level):
     S, H, _, _, _ = pair
-    f, c = H.levels[0], H.levels[1]
+    f, c = H.levels[level], H.levels[level + 1]
     phi = rand_unknowns(f, 7)
     s = rand_unknowns(f, 8)
     coarse = torch.zeros(c.n ** 3, dtype=torch.float64, device="cuda")
-    S.restrict_residual(0, dev(to_grid(f, phi)), dev(to_grid(f, s)), coarse)
-    t = MG.residual(H.ops[0], phi, s)
-    ref = MG.restrict(H.ops[0], H.ops[1], H.pmaps[0], t)
+    S.restrict_residual(level, dev(to_grid(f, phi)), dev(to_grid(f, s)), coarse)
+    t = MG.residual(H.ops[level], phi, s)
+    ref = MG.restrict(H.ops[level], H.ops[level + 1], H.pmaps[level], t)
     S.sync()
     assert rel(from_grid(c, coarse.cpu()), ref, np.abs(t).max()) < 1e-12
-    e = rand_unknowns(c, 9)
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_prolong_parity(pair, level):
+    """Trilinear (default) and patch-wise constant prolongation, both from every
+    coarse unknown into the phi1 cells."""
+    S, H, _, _, prob = pair
+    f, c = H.levels[level], H.levels[level + 1]
+    phi = rand_unknowns(f, 9)
+    e = rand_unknowns(c, 10)
     g = dev(to_grid(f, phi))
-    S.prolong_add(0, dev(to_grid(c, e)), g)
+    S.prolong_add(level, dev(to_grid(c, e)), g)
     S.sync()
-    ref = MG.prolong(H.ops[0], H.ops[1], H.pmaps[0], e, phi)
+    ref = MG.prolong_trilinear(H.ops[level], H.P[level], e, phi)
     assert rel(from_grid(f, g.cpu()), ref, np.abs(ref).max()) < 1e-14
+    K = solver(prob, prolong=0)
+    g = dev(to_grid(f, phi))
+    K.prolong_add(level, dev(to_grid(c, e)), g)
+    K.sync()
+    ref = MG.prolong(H.ops[level], H.ops[level + 1], H.pmaps[level], e, phi)
+    assert rel(from_grid(f, g.cpu()), ref, np.abs(ref).max()) < 1e-14
+    K.close()
 
 
 def test_bottom_parity(pair):
@@ -164,6 +204,7 @@ def test_bottom_parity(pair):
 
 
 def test_vcycle_parity(pair):
+    """One V-cycle through all three levels (recursion through level 16)."""
     S, H, _, r_or, _ = pair
     lv = H.levels[0]
     e = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
@@ -171,6 +212,40 @@ def test_vcycle_parity(pair):
     S.sync()
     ref = H.vcycle(0, r_or)
     assert rel(from_grid(lv, e.cpu()), ref, np.abs(ref).max()) < 1e-10
+
+
+def test_trajectory_parity(pair):
+    """Alg. Multigrid step by step: phi_{k+1} = phi_k + VCycle(r - L phi_k), the
+    residual and the V-cycle on the GPU, against the oracle's iterates, k = 1..4."""
+    S, H, _, r_or, _ = pair
+    lv = H.levels[0]
+    rg = dev(to_grid(lv, r_or))
+    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    s = torch.zeros_like(phi)
+    e = torch.zeros_like(phi)
+    ref = np.zeros(len(r_or))
+    for k in range(4):
+        S.residual(0, phi, rg, s, True)
+        S.vcycle(s, e)
+        S.sync()
+        phi += e
+        ref = ref + H.vcycle(0, MG.residual(H.ops[0], ref, r_or))
+        assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-10, k
+
+
+def test_fp32_vcycle_parity(pair):
+    """The FP32 V-cycle (precision 2: FP32 Jacobi, residual, restriction and
+    trilinear prolongation, FP32 LU-correction factors with double-float
+    right-hand sides, FP64 bottom solve) against the oracle's FP64 V-cycle."""
+    S, H, _, r_or, prob = pair
+    K = solver(prob, precision=2)
+    lv = H.levels[0]
+    e = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    K.vcycle(dev(to_grid(lv, r_or)), e)
+    K.sync()
+    ref = H.vcycle(0, r_or)
+    assert rel(from_grid(lv, e.cpu()), ref, np.abs(ref).max()) < 2e-5
+    K.close()
 
 
 def test_solve_parity(pair):
@@ -203,112 +278,3 @@ def test_solve_host_buffers(pair):
     phi_d = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
     st2, _ = S.solve(dev(f), dev(gb), dev(gp), phi_d)
     assert np.abs(phi - phi_d.cpu().numpy()).max() < 1e-12 * np.abs(phi).max()
-
-
-@pytest.mark.parametrize("cgs", [0, 1])
-@pytest.mark.parametrize("flexible", [0, 1])
-def test_gmres_acceleration(pair, flexible, cgs):
-    """GMRES right-preconditioned by the same V-cycle (plain, or flexible with the
-    preconditioned vectors kept; modified or classical Gram-Schmidt) reaches the
-    same discrete solution (the oracle's converged Alg. Multigrid) in fewer
-    V-cycles."""
-    from paper_2410_05865_gb300 import ccmg
-    S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, krylov=1, krylov_restart=30,
-                    krylov_flexible=flexible, krylov_cgs=cgs)
-    lv = H.levels[0]
-    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
-    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
-    assert rc == 0 and st.converged and st.rel_resid < 1e-10
-    ref, hist, it = H.multigrid(r_or, eps=1e-10)
-    assert st.iters < it
-    got = from_grid(lv, phi.cpu())
-    assert rel(got, ref, np.abs(ref).max()) < 1e-7
-    K.close()
-
-
-@pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("krylov", [0, 1])
-def test_mixed_precision_solve(pair, krylov, precision):
-    """FP32 grid work (precision 1), and also FP32 LU-correction factors
-    (precision 2), inside FP64 defect correction reach the FP64 1e-10 residual
-    and the oracle's converged solution."""
-    from paper_2410_05865_gb300 import ccmg
-    S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, precision=precision, krylov=krylov)
-    lv = H.levels[0]
-    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
-    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
-    assert rc == 0 and st.rel_resid < 1e-10
-    ref, hist, it = H.multigrid(r_or, eps=1e-10)
-    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
-    K.close()
-
-
-def test_bench_configuration_solve(pair):
-    """The configuration the benchmark runs (FP32 grid work and LU-correction
-    factors, flexible GMRES(30) with classical Gram-Schmidt, trilinear
-    prolongation, full-weighting restriction) reaches the oracle's converged
-    solution."""
-    from paper_2410_05865_gb300 import ccmg
-    S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, precision=2, krylov=1,
-                    krylov_restart=30, krylov_flexible=1, krylov_cgs=1, prolong=1, restriction=1)
-    lv = H.levels[0]
-    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
-    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
-    assert rc == 0 and st.converged and st.rel_resid < 1e-10
-    ref, hist, it = H.multigrid(r_or, eps=1e-10)
-    assert st.iters < it
-    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
-    K.close()
-
-
-def test_lu_schedules_agree(pair):
-    """The one-launch cooperative sweep schedule gives the same LU-correction as
-    one launch per tree height (to FP64 rounding of the atomic adds)."""
-    from paper_2410_05865_gb300 import ccmg
-    S, H, _, _, prob = pair
-    lv = H.levels[0]
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, lu_schedule=1)
-    phi = rand_unknowns(lv, 11)
-    s = rand_unknowns(lv, 12) * 1e3
-    a = dev(to_grid(lv, phi))
-    b = dev(to_grid(lv, phi))
-    S.lu_correction(0, a, dev(to_grid(lv, s)))
-    K.lu_correction(0, b, dev(to_grid(lv, s)))
-    S.sync()
-    K.sync()
-    ga, gb_ = a.cpu().numpy(), b.cpu().numpy()
-    assert np.abs(ga - gb_).max() < 1e-11 * np.abs(ga).max()
-    K.close()
-
-
-def test_smo1_tiles_tuned(pair):
-    """The set-up autotuner picks one of its candidate SMO-1 tiles for every
-    smoothed level (the Jacobi parity above runs with that tile)."""
-    S, H, _, _, _ = pair
-    cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4), (8, 8), (4, 32), (8, 32), (4, 64)}
-    for m in range(len(H.levels) - 1):
-        assert tuple(S.info.jacobi_block[m]) in cands
-
-
-@pytest.mark.parametrize("restriction", [0, 1])
-@pytest.mark.parametrize("krylov", [0, 1])
-def test_trilinear_prolongation_solve(pair, krylov, restriction):
-    """The trilinear prolongation and full-weighting restriction options change
-    only the V-cycle, not the discrete system: the solve reaches the oracle's
-    converged solution."""
-    from paper_2410_05865_gb300 import ccmg
-    S, H, (f, gb, gp), r_or, prob = pair
-    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, prolong=1, krylov=krylov,
-                    restriction=restriction)
-    lv = H.levels[0]
-    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
-    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
-    assert rc == 0 and st.rel_resid < 1e-10
-    ref, hist, it = H.multigrid(r_or, eps=1e-10)
-    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7
-    if krylov == 0:
-        assert st.iters < it  # fewer V-cycles than with the piecewise-constant prolongation
-    K.close()

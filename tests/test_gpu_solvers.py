@@ -1,0 +1,113 @@
+"""Solver options on the GPU against the oracle's converged solution (C ABI).
+
+The sphere configuration and the three-ellipsoid configuration (seed 0,
+Neumann on the ellipsoids) at 32^3, levels 32/16/8.  Every option changes how
+the discrete system is solved, never the system: each solve must reach the
+FP64 1e-10 relative residual and the oracle's converged Alg. Multigrid
+solution to 1e-7 relative (two stops at 1e-10 differ by up to
+1e-10 / (1 - factor) times cond(L)).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import discretization as D
+from oracle import multigrid as MG
+
+pytestmark = pytest.mark.gpu
+
+N = 32
+MIN_N = 8
+
+
+@pytest.fixture(scope="module", params=["sphere", "ellipsoids_neumann"])
+def case(request):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_05865_gb300 import ccmg
+    prob = W.sphere_problem(N) if request.param == "sphere" else W.ellipsoids_problem(N, 0)
+    S = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N)
+    f = ccmg.cell_averages(S, W.lap_phi_exact)
+    gb = ccmg.box_face_averages(S, W.phi_exact, W.grad_phi_exact, prob.box_bc)
+    gp = ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, prob.shape_bc)
+    S.close()
+    levels = D.build_hierarchy(N, prob.shapes, prob.shape_bc, prob.box_bc, min_n=MIN_N)
+    H = MG.Hierarchy(levels)
+    lv = levels[0]
+    r_or = lv.rhs(lv.cell_averages(W.lap_phi_exact), lv.box_face_averages(W.phi_exact, W.grad_phi_exact),
+                  lv.patch_averages(W.phi_exact, W.grad_phi_exact))
+    ref, hist, it = H.multigrid(r_or, eps=1e-10)
+    return prob, (f, gb, gp), lv, ref, it
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run(case, **kw):
+    from paper_2410_05865_gb300 import ccmg
+    prob, (f, gb, gp), lv, ref, it = case
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N, **kw)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    K.close()
+    got = phi.cpu().numpy()[lv.slots]
+    return st, rc, np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cgs", [0, 1])
+@pytest.mark.parametrize("flexible", [0, 1])
+def test_gmres_acceleration(case, flexible, cgs):
+    """GMRES right-preconditioned by the same V-cycle (plain, or flexible with the
+    preconditioned vectors kept; modified or classical Gram-Schmidt) reaches the
+    same discrete solution in no more V-cycles than Alg. Multigrid."""
+    st, rc, err = run(case, krylov=1, krylov_restart=30, krylov_flexible=flexible, krylov_cgs=cgs)
+    assert rc == 0 and st.converged and st.rel_resid < 1e-10
+    assert st.iters <= case[4]
+    assert err < 1e-7
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_mixed_precision_solve(case, krylov, precision):
+    """FP32 grid work (precision 1), and also FP32 LU-correction factors
+    (precision 2), inside FP64 defect correction reach the FP64 1e-10 residual
+    and the oracle's converged solution."""
+    st, rc, err = run(case, precision=precision, krylov=krylov)
+    assert rc == 0 and st.rel_resid < 1e-10
+    assert err < 1e-7
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("prolong", [0, 1])
+def test_transfer_options_solve(case, prolong, restriction):
+    """The prolongation (patch-wise constant / trilinear) and restriction (the
+    paper's 2^-3 sum / full weighting) options change only the V-cycle: the
+    stationary solve reaches the oracle's converged solution."""
+    st, rc, err = run(case, prolong=prolong, restriction=restriction)
+    assert rc == 0 and st.rel_resid < 1e-10
+    assert err < 1e-7
+    if prolong == 1 and restriction == 0:
+        assert abs(st.iters - case[4]) <= 1  # the oracle runs this V-cycle
+
+
+def test_lu_schedules_agree(case):
+    """The one-launch cooperative sweep schedule gives the same solve as one
+    launch per tree height."""
+    st, rc, err = run(case, lu_schedule=1)
+    assert rc == 0 and st.rel_resid < 1e-10
+    assert err < 1e-7
+
+
+def test_smo1_tiles_tuned(case):
+    """The set-up autotuner picks one of its candidate SMO-1 tiles for every
+    smoothed level."""
+    from paper_2410_05865_gb300 import ccmg
+    prob = case[0]
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N)
+    cands = {(16, 8), (32, 4), (8, 16), (16, 16), (32, 8), (64, 2), (64, 4), (8, 8), (4, 32), (8, 32), (4, 64)}
+    for m in range(K.info.n_levels - 1):
+        assert tuple(K.info.jacobi_block[m]) in cands
+    K.close()

@@ -1,8 +1,12 @@
 """The C-ABI library builds, loads and exports every symbol include/ccmg.h declares.
 
 Also checks the host-only setup (device < 0) against the oracle on CPU: cell
-classes, merging, the phi1/phi2 split and every phi2 row of both levels of the
-sphere configuration at 32^3 (same columns, coefficients to 1e-12 relative).
+classes, merging, the phi1/phi2 split, every phi2 row and its boundary terms
+(patches and box faces) on every level of two hierarchies at 32^3 with
+coarsening down to 8^3: the sphere configuration (Dirichlet) and the
+three-ellipsoid configuration (seed 0, Neumann on the ellipsoids), whose coarse
+levels have phi2 rows next to the box, merged cells and lower-degree rows.
+Same columns, coefficients to 1e-12 relative.
 """
 import os
 import re
@@ -66,12 +70,12 @@ def test_setup_error_message(ccmg):
     assert e.value.status == 1 and "semi-axis" in str(e.value)
 
 
-@pytest.fixture(scope="module")
-def host_pair(ccmg):
+@pytest.fixture(scope="module", params=["sphere", "ellipsoids_neumann"])
+def host_pair(request, ccmg):
     from oracle import discretization as D
-    prob = W.sphere_problem(32)
-    S = ccmg.Solver(32, prob.shapes, prob.shape_bc, prob.box_bc, device=-1)
-    levels = D.build_hierarchy(32, prob.shapes, prob.shape_bc, prob.box_bc)
+    prob = W.sphere_problem(32) if request.param == "sphere" else W.ellipsoids_problem(32, 0)
+    S = ccmg.Solver(32, prob.shapes, prob.shape_bc, prob.box_bc, device=-1, min_coarse_n=8)
+    levels = D.build_hierarchy(32, prob.shapes, prob.shape_bc, prob.box_bc, min_n=8)
     return S, levels
 
 
@@ -100,7 +104,8 @@ def test_host_setup_matches_oracle(host_pair):
 
 
 def test_host_patch_terms_match_oracle(host_pair, ccmg):
-    """Boundary coefficients of the phi2 rows (the N g part of r = f - N g)."""
+    """Boundary coefficients of the phi2 rows (the N g part of r = f - N g):
+    patch terms and box-face terms (code -(1 + face id))."""
     S, levels = host_pair
     lv = levels[0]
     cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(0)
@@ -108,12 +113,25 @@ def test_host_patch_terms_match_oracle(host_pair, ccmg):
     L = lv.L.tocsr()
     for r, c in enumerate(cells):
         u = lv.uid[c]
-        ref = {key[1]: v for key, v in lv.gcoef[u]}
-        got = {int(owners[bpatch[q]]): bcoef[q] for q in range(bptr[r], bptr[r + 1])}
+        ref = {key: v for key, v in lv.gcoef[u]}
+        got = {}
+        for q in range(bptr[r], bptr[r + 1]):
+            b = int(bpatch[q])
+            key = ("patch", int(owners[b])) if b >= 0 else ("box", -1 - b)
+            got[key] = bcoef[q]
         assert set(ref) == set(got)
         scale = np.abs(L.data[L.indptr[u]:L.indptr[u + 1]]).max()  # the row's scale
         for k in ref:
             assert abs(ref[k] - got[k]) < 1e-12 * scale
+
+
+def test_box_face_terms_present(ccmg):
+    """The three-ellipsoid geometry of seed 0 comes within 0.08 of a wall: at
+    16^3 its phi2 rows reach the box, and their fits carry box-face terms."""
+    prob = W.ellipsoids_problem(16, 0)
+    S = ccmg.Solver(16, prob.shapes, prob.shape_bc, prob.box_bc, device=-1, min_coarse_n=16)
+    cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(0)
+    assert (bpatch < 0).sum() > 0
 
 
 def test_host_lu_block_forms(host_pair):

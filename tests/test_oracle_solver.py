@@ -68,10 +68,35 @@ def test_transfers_on_constants(small):
     np.add.at(kids, pm[f.i1], 1)
     assert np.allclose(sc[kids == 8], 1.0)
     e = np.full(len(sc), 2.5)
+    # patch-wise constant: every phi1 cell under a coarse unknown gets the value
     out = MG.prolong(f, c, pm, e, np.zeros(len(t)))
     assert np.allclose(out[f.i2], 0.0)
-    parent_phi1 = np.isin(pm[f.i1], c.i1)
-    assert np.allclose(out[f.i1][parent_phi1], 2.5) and np.allclose(out[f.i1][~parent_phi1], 0.0)
+    assert np.allclose(out[f.i1][pm[f.i1] >= 0], 2.5)
+    # trilinear: the renormalised weights reproduce constants on every phi1 cell
+    out = MG.prolong_trilinear(f, H.P[0], e, np.zeros(len(t)))
+    assert np.allclose(out[f.i2], 0.0)
+    assert np.allclose(out[f.i1], 2.5, rtol=0, atol=1e-14)
+
+
+def test_trilinear_prolongation_linear_fields(small):
+    """Cell-centred trilinear interpolation is exact for linear fields: the
+    coarse averages of x + 2y - 3z prolongate to the fine averages wherever all
+    8 coarse neighbours are full coarse unknowns (cell averages of a linear
+    field are its centre values)."""
+    H, _ = small
+    fl, cl = H.levels[0], H.levels[1]
+    lin = lambda lv, o: np.dot(lv.coords(int(o)) + 0.5, [1.0, 2.0, -3.0]) * lv.h
+    ec = np.array([lin(cl, o) for o in cl.slots])
+    out = MG.prolong_trilinear(H.ops[0], H.P[0], ec, np.zeros(len(fl.slots)))
+    P = H.P[0].tocsr()
+    full_c = (cl.kind[cl.slots] == 1)
+    checked = 0
+    for r in H.ops[0].i1:
+        cols = P.indices[P.indptr[r]:P.indptr[r + 1]]
+        if len(cols) == 8 and full_c[cols].all():
+            assert abs(out[r] - lin(fl, fl.slots[r])) < 1e-14
+            checked += 1
+    assert checked > 1000
 
 
 def test_fmg_algebraic_error_decreases(small):

@@ -1,21 +1,26 @@
-"""Benchmark: time to a 1e-10 relative residual for the fourth-order cut-cell
-multigrid solve at 256^3 (three overlapping ellipsoids, Dirichlet on the box,
-manufactured solution), on one GB300.  The ellipsoids carry Dirichlet data by
-default (--shape-bc dirichlet): with Neumann data on these ellipsoids at 256^3
-the phi2 block L22 of the finest level is close to singular and the V-cycle
-does not converge (--shape-bc neumann runs that case).
+"""Benchmark: time to a 1e-10 relative residual of the fourth-order cut-cell
+multigrid solve at 256^3 on one GB300, on the three-ellipsoid workload as it
+is stated: [0,1]^3 minus three overlapping ellipsoids (seeds 0-4), Neumann
+data on the ellipsoids, Dirichlet on the box, manufactured solution.
 
-One step = one whole solve (Alg. Multigrid from a zero start, every V-cycle
-with SMO-1, SMO-2, Restrict, Prolong and the bottom solve) of the same
-synthetic input, whose arrays are resident in HBM when the timed region starts.
-The solver working set (grids, phi2 rows, LU factors: several GB) is far
-larger than the 129 MB L2, so no L2 flush is needed between steps.
+One step = one whole solve of every seed (Alg. Multigrid from a zero start,
+every V-cycle with SMO-1, SMO-2, Restrict, Prolong and the bottom solve) on
+inputs resident in HBM when the timed region starts.  The headline solver is
+the V-cycle in mixed precision (FP32 smoothing, residuals and transfers inside
+FP64 defect correction; FP64 LU-corrections, PLG rows, bottom solve and outer
+residual).  The solver working set (grids, phi2 rows, LU factors: GBs per
+seed) is far larger than the 129 MB L2, so no L2 flush is needed.
 
-value  = unknowns x replicas / seconds per solve, in MDOF/s (higher is better)
+value  = unknowns of all seeds x replicas / seconds per step, in MDOF/s
 e2e    = the same through cc_solve with pinned host buffers (H2D of f, g and
          the initial guess, D2H of phi inside the timed region)
+The line also carries, measured in the same run: the plain FP64 V-cycle (the
+metric's reference), labelled variants (FP32 LU-correction factors, flexible
+GMRES around the V-cycle), the relative difference of each solution from the
+FP64 one, the error against the manufactured cell averages and the
+convergence order over 64^3/128^3/256^3.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (see cpu_baseline) on the host cores.
+workload on the host cores.
 
 Multi-GPU: the path does not shard (replicas only): each rank solves its own
 copy; value sums the replicas' unknowns over the slowest rank's time.
@@ -30,6 +35,10 @@ import subprocess
 import sys
 import threading
 import time
+
+if "reference" in sys.argv:  # the oracle's timed solve runs on one host core: no BLAS thread pool
+    for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(_k, "1")
 
 import numpy as np
 
@@ -46,40 +55,45 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-n", type=int, default=64, help="grid of the oracle's CPU sample")
-    ap.add_argument("--precision", type=int, default=2,
+    ap.add_argument("--seeds", default="0,1,2,3,4", help="ellipsoid seeds solved in one step")
+    ap.add_argument("--cpu-n", type=int, default=32, help="grid of the oracle's CPU sample")
+    ap.add_argument("--precision", type=int, default=1,
                     help="0 FP64 V-cycle; 1 FP32 grid work, FP64 LU-corrections; 2 FP32 grid work and "
                          "LU-correction factors (their PLG right-hand sides in double-float; FP64 bottom "
                          "solve and outer residual)")
-    ap.add_argument("--krylov", type=int, default=1, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
-    ap.add_argument("--min-n", type=int, default=32, help="coarsening stops before n < min-n")
+    ap.add_argument("--krylov", type=int, default=0, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
+    ap.add_argument("--min-n", type=int, default=16, help="coarsening stops before n < min-n")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--prolong", type=int, default=1,
-                    help="0 the paper's piecewise-constant prolongation; 1 trilinear cell-centred")
-    ap.add_argument("--restriction", type=int, default=1,
+                    help="0 piecewise-constant prolongation (the printed Prolong); 1 trilinear cell-centred")
+    ap.add_argument("--restriction", type=int, default=0,
                     help="0 the paper's 2^-3 sum over the children; 1 full weighting")
     ap.add_argument("--cgs", type=int, default=1,
                     help="GMRES orthogonalisation: 0 modified, 1 classical Gram-Schmidt (two fused passes)")
-    ap.add_argument("--no-fp64-reference", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 reference, variants and order runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--shape-bc", default="dirichlet", choices=["dirichlet", "neumann"],
+    ap.add_argument("--shape-bc", default="neumann", choices=["dirichlet", "neumann"],
                     help="boundary kind on the ellipsoids (the box is Dirichlet)")
     ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="single: the 256^3 solve; batch: --batch independent solves of mixed sizes")
+                    help="single: the 256^3 solves; batch: --batch independent solves of mixed sizes")
     ap.add_argument("--batch", type=int, default=16, help="solves in the batch workload")
+    ap.add_argument("--seed", type=int, default=0, help="first seed of the batch workload")
     return ap.parse_args()
 
 
-def problem(W, n, args):
+def seeds_of(args):
+    return [int(x) for x in args.seeds.split(",") if x.strip() != ""]
+
+
+def problem(W, n, seed, args):
     """The three-ellipsoid geometry of the seed, with the chosen kind on the shapes."""
-    prob = W.ellipsoids_problem(n, args.seed)
+    prob = W.ellipsoids_problem(n, seed)
     prob.shape_bc = W.DIRICHLET if args.shape_bc == "dirichlet" else W.NEUMANN
     return prob
 
 
 def workload(args, n):
-    return (f"three overlapping ellipsoids (seed {args.seed}) at {n}^3, {args.shape_bc.capitalize()} on the "
+    return (f"three overlapping ellipsoids (seeds {args.seeds}) at {n}^3, {args.shape_bc.capitalize()} on the "
             f"ellipsoids, Dirichlet on the box, manufactured phi, zero start, to 1e-10 relative residual")
 
 
@@ -170,36 +184,82 @@ def make_inputs(ccmg, W, S, prob):
     return f, gb, gp
 
 
-def cpu_baseline(args, v_cycles):
-    """The oracle, as it stands, on the same geometry and boundary kinds at a
-    smaller grid: a few V-cycles are timed on one host core and scaled to the
-    V-cycle count of the timed GPU solve (unknowns per second through the same
-    number of V-cycles)."""
+def _oracle_problem(n, seed, shape_bc):
+    """The oracle's hierarchy and right-hand side of one seed (setup, untimed)."""
     import workloads as W
     from oracle import discretization as D
     from oracle import multigrid as MG
-    n = args.cpu_n
-    prob = problem(W, n, args)
-    t0 = time.time()
+    prob = W.ellipsoids_problem(n, seed)
+    prob.shape_bc = shape_bc
     levels = D.build_hierarchy(n, prob.shapes, prob.shape_bc, prob.box_bc)
     H = MG.Hierarchy(levels)
     lv = levels[0]
     r = lv.rhs(lv.cell_averages(W.lap_phi_exact), lv.box_face_averages(W.phi_exact, W.grad_phi_exact),
                lv.patch_averages(W.phi_exact, W.grad_phi_exact))
-    setup_s = time.time() - t0
-    phi = np.zeros_like(r)
-    k = 3
+    return H, r
+
+
+_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(task):
+    """One oracle solve in a worker process: build, wait for every worker, then
+    time the whole Alg. Multigrid solve to 1e-10 from a zero start."""
+    n, seed, shape_bc = task
+    H, r = _oracle_problem(n, seed, shape_bc)
+    if _BARRIER is not None:
+        _BARRIER.wait()
     t0 = time.time()
-    for _ in range(k):
-        s = MG.residual(H.ops[0], phi, r)
-        phi = phi + H.vcycle(0, s)
-    per_cycle = (time.time() - t0) / k
-    N = len(lv.slots)
-    value = N / (per_cycle * v_cycles) / 1e6
-    return {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle FP64 (numpy/scipy, one core) on the same geometry and boundary kinds at {n}^3 "
-                       f"({N} unknowns): {k} V-cycles timed, {per_cycle*1e3:.0f} ms each, scaled by the "
-                       f"{v_cycles} V-cycles of the timed GPU solve; oracle setup {setup_s:.0f} s not timed")}
+    _, hist, iters = H.multigrid(r, eps=1e-10, imax=400)
+    t1 = time.time()
+    return {"N": len(r), "t0": t0, "t1": t1, "iters": iters}
+
+
+def cpu_baseline(args):
+    """The oracle, as it stands, on the same geometry and boundary kinds at a
+    smaller grid, whole solves to 1e-10: one solve on one host core, then one
+    solve per host core at once (spawned processes, seeds cycled, all started
+    together after their setups), unknowns per second over the wall time."""
+    import multiprocessing as mp
+    import workloads as W
+    seeds = seeds_of(args)
+    bc = W.DIRICHLET if args.shape_bc == "dirichlet" else W.NEUMANN
+    n = args.cpu_n
+    H, r = _oracle_problem(n, seeds[0], bc)
+    t0 = time.time()
+    _, hist, iters = H.multigrid(r, eps=1e-10, imax=400)
+    dt1 = time.time() - t0
+    N = len(r)
+    one = N / dt1 / 1e6
+    cores = os.cpu_count() or 1
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        bar = ctx.Barrier(cores)
+        with ctx.Pool(cores, initializer=_pool_init, initargs=(bar,)) as pool:
+            res = pool.map(_oracle_worker, [(n, seeds[k % len(seeds)], bc) for k in range(cores)])
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    wall = max(x["t1"] for x in res) - min(x["t0"] for x in res)
+    allc = sum(x["N"] for x in res) / wall / 1e6
+    return {"value": one, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 (numpy/scipy) on the same geometry and boundary kinds at {n}^3 "
+                       f"(seed {seeds[0]}, {N} unknowns): one whole Alg. Multigrid solve to 1e-10 from zero "
+                       f"({iters} V-cycles, {dt1:.2f} s) on one host core; setup not timed"),
+            "all_cores": {"value": allc, "unit": "MDOF/s", "cores": cores,
+                          "sample": (f"{cores} such solves at once (seeds {seeds} cycled), one spawned process "
+                                     f"per core, {wall:.2f} s wall from the first start to the last finish")}}
 
 
 def run_reference(args):
@@ -207,45 +267,51 @@ def run_reference(args):
     if rank != 0:
         return
     import workloads as W
-    from oracle import discretization as D
-    from oracle import multigrid as MG
+    bc = W.DIRICHLET if args.shape_bc == "dirichlet" else W.NEUMANN
+    seeds = seeds_of(args)
     n = args.cpu_n
-    prob = problem(W, n, args)
-    levels = D.build_hierarchy(n, prob.shapes, prob.shape_bc, prob.box_bc)
-    H = MG.Hierarchy(levels)
-    lv = levels[0]
-    r = lv.rhs(lv.cell_averages(W.lap_phi_exact), lv.box_face_averages(W.phi_exact, W.grad_phi_exact),
-               lv.patch_averages(W.phi_exact, W.grad_phi_exact))
-    N = len(lv.slots)
-    # a step: 3 V-cycles of the oracle; the metric scales them to a whole solve
-    # using the oracle's own iteration count at this grid (measured once, untimed)
-    _, hist, iters = H.multigrid(r, eps=1e-10, imax=400)
-    phi = np.zeros_like(r)
+    H, r = _oracle_problem(n, seeds[0], bc)
+    N = len(r)
+    iters = [0]
 
-    def step():
-        nonlocal phi
-        for _ in range(3):
-            s = MG.residual(H.ops[0], phi, r)
-            phi = phi + H.vcycle(0, s)
+    def step():  # one whole oracle solve to 1e-10 from a zero start
+        _, hist, it = H.multigrid(r, eps=1e-10, imax=400)
+        iters[0] = it
 
     for _ in range(args.warmup):
         step()
     t0 = time.time()
     for _ in range(args.steps):
         step()
-    dt = (time.time() - t0) / args.steps / 3.0
-    value = N / (dt * iters) / 1e6
-    sample = (f"oracle FP64 (one core) on the same geometry and boundary kinds at {n}^3, {N} unknowns; "
-              f"a step = 3 V-cycles ({dt*1e3:.0f} ms each), scaled by the oracle's {iters} V-cycles to 1e-10")
+    dt = (time.time() - t0) / args.steps
+    value = N / dt / 1e6
+    sample = (f"oracle FP64 (numpy/scipy, one core) on the same geometry and boundary kinds at {n}^3 (seed "
+              f"{seeds[0]}, {N} unknowns); a step = one whole Alg. Multigrid solve to 1e-10 from zero "
+              f"({iters[0]} V-cycles), measured")
     print(json.dumps({"metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": args.gpus,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * iters * 1e3,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "impl": "reference",
-                      "config": {"workload": workload(args, args.n) + f" (CPU sample at {n}^3)",
-                                 "n": n, "unknowns": N},
+                      "config": {"workload": workload(args, args.n) + f" (CPU sample at {n}^3, seed {seeds[0]})",
+                                 "n": n, "unknowns": N, "v_cycles": iters[0]},
                       "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def _solve_all(solvers, inputs, phis):
+    its = []
+    for S, x, phi in zip(solvers, inputs, phis):
+        phi.zero_()
+        st, rc = S.solve(*x, phi)
+        if rc != 0:
+            raise RuntimeError(f"solve did not converge: status {rc}, rel {st.rel_resid}")
+        its.append(st.iters)
+    return its
+
+
+def _exact_averages(ccmg, W, S):
+    return ccmg.cell_averages_terms(S, W.phi_terms())
 
 
 def run_ours(args):
@@ -257,31 +323,30 @@ def run_ours(args):
     world, rank, local = dist_init(args)
     torch.cuda.set_device(local)
     n = args.n
-    prob = problem(W, n, args)
-    t0 = time.time()
-    solver_kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n,
-                     krylov_restart=args.restart, max_iter=2000, prolong=args.prolong,
-                     restriction=args.restriction, krylov_cgs=args.cgs)
-    S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **solver_kw)
-    setup_s = time.time() - t0
+    seeds = seeds_of(args)
+    kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n, krylov_restart=args.restart,
+              max_iter=2000, prolong=args.prolong, restriction=args.restriction, krylov_cgs=args.cgs)
     stream = torch.cuda.Stream()
-    S.set_stream(stream)
-    f, gb, gp = make_inputs(ccmg, W, S, prob)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    fd, gbd, gpd = dev(f), dev(gb), dev(gp)
-    phi = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
-    N = S.info.n_unknowns[0]
-
-    def step():
-        phi.zero_()
-        st, rc = S.solve(fd, gbd, gpd, phi)
-        if rc != 0:
-            raise RuntimeError(f"solve did not converge: status {rc}, rel {st.rel_resid}")
-        return st
+    probs, solvers, inputs, host_inputs, phis, setup_s = [], [], [], [], [], []
+    for sd in seeds:
+        prob = problem(W, n, sd, args)
+        t0 = time.time()
+        S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **kw)
+        setup_s.append(round(time.time() - t0, 1))
+        S.set_stream(stream)
+        f, gb, gp = make_inputs(ccmg, W, S, prob)
+        probs.append(prob)
+        solvers.append(S)
+        host_inputs.append((f, gb, gp))
+        inputs.append((dev(f), dev(gb), dev(gp)))
+        phis.append(torch.zeros(n ** 3, dtype=torch.float64, device="cuda"))
+    Ns = [S.info.n_unknowns[0] for S in solvers]
+    Ntot = sum(Ns)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            st = step()
+            _solve_all(solvers, inputs, phis)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -293,119 +358,223 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         ev0.record(stream)
         for _ in range(args.steps):
-            st = step()
-            iters.append(st.iters)
+            iters = _solve_all(solvers, inputs, phis)
         ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ms = ev0.elapsed_time(ev1) / args.steps
     ck = clocks.stop()
     ms = max_over_ranks(ms, world)
-    value = N * world / (ms / 1e3) / 1e6
+    value = Ntot * world / (ms / 1e3) / 1e6
+    per_seed_ms, head_stats = [], []
+    with torch.cuda.stream(stream):  # per-seed solve times (library events), one more solve each
+        for S, x, phi in zip(solvers, inputs, phis):
+            phi.zero_()
+            st, _ = S.solve(*x, phi)
+            per_seed_ms.append(round(st.ms_solve, 2))
+            head_stats.append((st.iters,) + _factors(st))
+    torch.cuda.synchronize()
+    phi_head = [ph.cpu().numpy() for ph in phis]
 
     # e2e: the public C ABI with pinned host buffers (copies inside the timed region)
-    fh = torch.from_numpy(f).pin_memory()
-    gbh = torch.from_numpy(gb).pin_memory()
-    gph = torch.from_numpy(gp).pin_memory()
-    phih = torch.zeros(n ** 3, dtype=torch.float64).pin_memory()
+    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in hx) for hx in host_inputs]
+    phih = [torch.zeros(n ** 3, dtype=torch.float64).pin_memory() for _ in seeds]
     with torch.cuda.stream(stream):
-        S.solve(fh, gbh, gph, phih, where=ccmg.CC_HOST)
+        for S, x, ph in zip(solvers, pinned, phih):
+            S.solve(*x, ph, where=ccmg.CC_HOST)
     torch.cuda.synchronize()
     t_e = time.perf_counter()
     for _ in range(args.steps):
-        phih.zero_()
-        st_e, rc = S.solve(fh, gbh, gph, phih, where=ccmg.CC_HOST)
-        if rc != 0:
-            raise RuntimeError("e2e solve failed")
+        for S, x, ph in zip(solvers, pinned, phih):
+            ph.zero_()
+            st_e, rc = S.solve(*x, ph, where=ccmg.CC_HOST)
+            if rc != 0:
+                raise RuntimeError("e2e solve failed")
     torch.cuda.synchronize()
     ms_e = (time.perf_counter() - t_e) * 1e3 / args.steps
     ms_e = max_over_ranks(ms_e, world)
-    h2d = int(fh.numel() * 8 + gbh.numel() * 8 + gph.numel() * 8 + phih.numel() * 8)
-    d2h = int(phih.numel() * 8)
+    h2d = int(sum(sum(a.numel() * 8 for a in x) + ph.numel() * 8 for x, ph in zip(pinned, phih)))
+    d2h = int(sum(ph.numel() * 8 for ph in phih))
 
-    # per-kernel profile of one solve: CUDA events around every launch, recorded
-    # inside the captured graphs (the same launch sequence as the timed solves)
-    S.profile(True)
+    # per-kernel profile of one solve of each seed: CUDA events around every
+    # launch, recorded inside the captured graphs (the timed launch sequence)
+    prof = {}
+    prof_iters = 0
     with torch.cuda.stream(stream):
-        st_p = step()
-    torch.cuda.synchronize()
-    prof = S.profile_entries()
-    S.profile(False)
-    # launches of one profiled solve, scaled to the timed steps by their V-cycle counts
-    launches = sum(v[0] for v in prof.values()) * sum(iters) / max(1, st_p.iters)
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (cnt, kms, kbytes) = top
+        for S, x, phi in zip(solvers, inputs, phis):
+            S.profile(True)
+            phi.zero_()
+            st_p, _ = S.solve(*x, phi)
+            torch.cuda.synchronize()
+            for k, v in S.profile_entries().items():
+                a = prof.get(k, (0, 0.0, 0.0))
+                prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
+            prof_iters += st_p.iters
+            S.profile(False)
+    launches = sum(v[0] for v in prof.values()) * sum(iters) / max(1, prof_iters) * args.steps
+    name, (cnt, kms, kbytes) = max(prof.items(), key=lambda kv: kv[1][1])
     hbm, src = peaks()
     achieved = (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else 0.0
     total_ms = sum(v[1] for v in prof.values())
     shares = {k: round(v[1] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]}
+    regular = ("jacobi", "resid_phi1", "restrict", "prolong")
+    reg_ms = sum(prof[k][1] for k in regular if k in prof)
+    reg_bytes = sum(prof[k][2] for k in regular if k in prof)
 
-    # the same solve with the FP64 V-cycle (the plain-FP64 reference of the metric)
-    fp64 = None
-    if args.precision != 0 and not args.no_fp64_reference:
-        kw = dict(solver_kw, precision=0)
-        S64 = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **kw)
-        S64.set_stream(stream)
-        with torch.cuda.stream(stream):
-            phi.zero_()
-            S64.solve(fd, gbd, gpd, phi)
-            phi.zero_()
-            st64, rc64 = S64.solve(fd, gbd, gpd, phi)
-        torch.cuda.synchronize()
-        fp64 = {"ms": st64.ms_solve, "v_cycles": st64.iters, "converged": bool(st64.converged),
-                "mdof_s": N / (st64.ms_solve / 1e3) / 1e6}
-        S64.close()
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(args, ccmg, W, torch, stream, probs, inputs, phi_head, head_stats, Ns, kw)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(args, iters[-1])
+            cpu = cpu_baseline(args)
         except Exception as exc:  # the baseline is context; report why it is missing
             cpu = {"value": None, "unit": "MDOF/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
     if rank == 0:
-        info = S.info
+        info = solvers[0].info
         out = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic",
-            "config": {"workload": workload(args, n),
-                       "n": n, "unknowns": N, "levels": [info.n[m] for m in range(info.n_levels)],
-                       "phi2_per_level": [info.n_phi2[m] for m in range(info.n_levels)],
-                       "lu_entries_per_level": [info.lu_entries[m] for m in range(info.n_levels)],
-                       "smo1_tiles_tuned": [[2 * info.jacobi_block[m][0], info.jacobi_block[m][1]]
-                                            for m in range(info.n_levels - 1)],
-                       "v_cycles": iters[-1], "omega": 0.5, "nu1": 3, "nu2": 3,
+            "config": {"workload": workload(args, n), "n": n, "seeds": seeds, "unknowns_per_seed": Ns,
+                       "unknowns": Ntot, "ms_per_solve": per_seed_ms,
+                       "mean_ms_to_1e-10_per_solve": round(ms / len(seeds), 2),
+                       "levels": [info.n[m] for m in range(info.n_levels)],
+                       "phi2_per_level_seed0": [info.n_phi2[m] for m in range(info.n_levels)],
+                       "lu_entries_per_level_seed0": [info.lu_entries[m] for m in range(info.n_levels)],
+                       "v_cycles": iters, "factor_mean_per_seed": [h[1] for h in head_stats],
+                       "factor_asymptotic_per_seed": [h[2] for h in head_stats], "omega": 0.5, "nu1": 3, "nu2": 3,
                        "precision": ["fp64",
-                                     "fp32 grid work; fp64 LU-corrections, bottom solve, outer residual",
+                                     "fp32 smoothing, residuals and transfers inside fp64 defect correction; fp64 "
+                                     "LU-corrections, PLG rows, bottom solve and outer residual",
                                      "fp32 grid work and LU-correction factors (PLG right-hand sides in "
                                      "double-float); fp64 bottom solve, outer residual"][args.precision],
-                       "outer": ["Alg. Multigrid",
+                       "outer": ["Alg. Multigrid (stationary)",
                                  f"flexible GMRES({args.restart}) preconditioned by the V-cycle, "
                                  f"{['modified', 'classical'][args.cgs]} Gram-Schmidt"][args.krylov],
-                       "prolongation": ["piecewise constant (the paper's Prolong)",
-                                        "trilinear cell-centred over coarse phi1 cells"][args.prolong],
+                       "prolongation": ["piecewise constant from every coarse unknown",
+                                        "trilinear cell-centred from every coarse unknown"][args.prolong],
                        "restriction": ["2^-3 sum over the phi1 children (the paper's Restrict)",
                                        "full weighting (transpose of trilinear / 8)"][args.restriction],
-                       "plain_fp64_same_solver": fp64,
-                       "setup_s": round(setup_s, 1), "parallelism": f"replicas x{world}",
-                       "l2": "no flush: working set of several GB > 129 MB L2"},
-            "e2e": {"value": N * world / (ms_e / 1e3) / 1e6, "unit": "MDOF/s", "ms_per_step": ms_e,
+                       "setup_s_per_seed": setup_s, "parallelism": f"replicas x{world}",
+                       "l2": "no flush: working set of several GB per seed > 129 MB L2"},
+            "e2e": {"value": Ntot * world / (ms_e / 1e3) / 1e6, "unit": "MDOF/s", "ms_per_step": ms_e,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "peak_source": src,
                          "bytes_per_launch": kbytes / max(1, cnt), "launches": cnt, "ms": kms},
+            "roofline_regular_part": {"kernels": list(regular), "achieved": reg_bytes / (reg_ms / 1e3) / 1e9
+                                      if reg_ms > 0 else 0.0, "peak": hbm, "unit": "GB/s",
+                                      "frac": (reg_bytes / (reg_ms / 1e3) / 1e9) / hbm if reg_ms > 0 else 0.0,
+                                      "ms": reg_ms, "bytes": reg_bytes},
             "kernel_time_share": shares,
             "clocks": ck,
         }
+        out["config"].update(extras)
         if cpu:
             out["cpu_baseline"] = cpu
         print(json.dumps(out))
-    S.close()
+    for S in solvers:
+        S.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _factors(st):
+    h = np.array(st.resid_hist[:min(st.iters, 256)])
+    mean = float(st.rel_resid ** (1.0 / max(1, st.iters)))
+    tail = h[1:] / h[:-1] if len(h) > 2 else np.array([mean])
+    return round(mean, 4), round(float(np.exp(np.log(tail[-6:]).mean())), 4)
+
+
+def run_extras(args, ccmg, W, torch, stream, probs, inputs, phi_head, head_stats, Ns, kw):
+    """Untimed-loop solves beside the headline, each timed by the library's
+    CUDA events around the solve: the plain FP64 V-cycle of every seed, labelled
+    variants on the first seed, and the convergence order of the first seed."""
+    n = args.n
+    local = torch.cuda.current_device()
+    phi = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+
+    def solve_with(prob, x, **over):
+        S = ccmg.Solver(n if over.get("_n") is None else over["_n"], prob.shapes, prob.shape_bc, prob.box_bc,
+                        device=local, **{k: v for k, v in dict(kw, **over).items() if k != "_n"})
+        S.set_stream(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(2):  # the second solve is the measured one
+                phi.zero_()
+                st, rc = S.solve(*x, phi)
+        torch.cuda.synchronize()
+        out = phi.cpu().numpy().copy()
+        return S, st, rc, out
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    fp64 = {"ms": [], "v_cycles": [], "converged": [], "rel_diff_headline_vs_fp64": [],
+            "max_err_vs_exact_fp64": [], "max_err_vs_exact_headline": [], "factor_mean": [], "factor_asymptotic": []}
+    phi64_0 = None
+    exact0 = None
+    for k, (prob, x) in enumerate(zip(probs, inputs)):
+        S, st, rc, p64 = solve_with(prob, x, precision=0)
+        ex = _exact_averages(ccmg, W, S)
+        mask = ex != 0.0
+        fp64["ms"].append(round(st.ms_solve, 2))
+        fp64["v_cycles"].append(st.iters)
+        fp64["converged"].append(bool(rc == 0))
+        fp64["rel_diff_headline_vs_fp64"].append(rel(phi_head[k], p64))
+        fp64["max_err_vs_exact_fp64"].append(float(np.abs(p64 - ex)[mask].max()))
+        fp64["max_err_vs_exact_headline"].append(float(np.abs(phi_head[k] - ex)[mask].max()))
+        fm, fa = _factors(st)
+        fp64["factor_mean"].append(fm)
+        fp64["factor_asymptotic"].append(fa)
+        if k == 0:
+            phi64_0, exact0 = p64, ex
+        S.close()
+    fp64["ms_all_seeds"] = round(sum(fp64["ms"]), 2)
+    fp64["mdof_s"] = sum(Ns) / (sum(fp64["ms"]) / 1e3) / 1e6
+    fp64["what"] = "the same Alg. Multigrid and V-cycle in FP64 throughout (precision 0)"
+
+    variants = {}
+    mask0 = exact0 != 0.0
+    for name, over, what in (
+            ("fp32_lu_factors", dict(precision=2, krylov=0),
+             "Alg. Multigrid, FP32 grid work and FP32 LU-correction factors (precision 2)"),
+            ("fgmres_fp32_lu_factors", dict(precision=2, krylov=1),
+             f"flexible GMRES({args.restart}) around the V-cycle of precision 2"),
+            ("fgmres_fp64", dict(precision=0, krylov=1), f"flexible GMRES({args.restart}) around the FP64 V-cycle")):
+        S, st, rc, pv = solve_with(probs[0], inputs[0], **over)
+        variants[name] = {"what": what, "ms": round(st.ms_solve, 2), "v_cycles": st.iters, "converged": rc == 0,
+                          "mdof_s": Ns[0] / (st.ms_solve / 1e3) / 1e6,
+                          "rel_diff_vs_fp64": rel(pv, phi64_0),
+                          "max_err_vs_exact": float(np.abs(pv - exact0)[mask0].max())}
+        S.close()
+
+    conv = {}
+    errs = []
+    for m in (64, 128):
+        prob = problem(W, m, seeds_of(args)[0], args)
+        Sx = ccmg.Solver(m, prob.shapes, prob.shape_bc, prob.box_bc, device=local, **kw)
+        f, gb, gp = make_inputs(ccmg, W, Sx, prob)
+        ex = _exact_averages(ccmg, W, Sx)
+        Sx.close()
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        S, st, rc, pm = solve_with(prob, (dev(f), dev(gb), dev(gp)), _n=m)
+        e = float(np.abs(pm - ex)[ex != 0.0].max())
+        errs.append(e)
+        fm, fa = _factors(st)
+        conv[str(m)] = {"v_cycles": st.iters, "factor_mean": fm, "factor_asymptotic": fa, "max_err": e,
+                        "ms": round(st.ms_solve, 2)}
+        S.close()
+    e256 = fp64["max_err_vs_exact_headline"][0]
+    errs.append(e256)
+    conv[str(n)] = {"v_cycles": head_stats[0][0], "factor_mean": head_stats[0][1],
+                    "factor_asymptotic": head_stats[0][2], "max_err": e256}
+    conv["order_max_err"] = [round(float(np.log2(errs[i] / errs[i + 1])), 2) for i in range(len(errs) - 1)]
+    return {"plain_fp64": fp64, "variants_seed0": variants, "convergence_seed0": conv}
 
 
 def run_batch(args):

@@ -8,8 +8,9 @@
  * averages <<g>>_i on the irregular boundary (Sec. 2.3-2.4).  The discrete
  * system L phi = r := f - N g (Sec. 2.4) is solved by Alg. Multigrid with
  * Alg. VCycle (Sec. 5.3): omega-Jacobi on phi1 (SMO-1) + LU-correction on phi2
- * (SMO-2), restriction by the 2^-3 sum over phi1 children, piecewise-constant
- * prolongation of the coarse phi1 corrections, and a direct bottom solve.
+ * (SMO-2), restriction by the 2^-3 sum over phi1 children, prolongation of the
+ * coarse corrections into the phi1 cells (trilinear by default, the printed
+ * patch-wise constant one as an option), and a direct bottom solve.
  *
  * Conventions
  *  - A grid array of level m has n_m^3 doubles, index (i*n_m + j)*n_m + k for
@@ -97,9 +98,13 @@ typedef struct {
   int krylov_cgs;    /* GMRES orthogonalisation: 0 modified Gram-Schmidt (a dot and an
                         update per basis vector); 1 classical Gram-Schmidt in two
                         fused passes over the basis (0) */
-  int prolong;       /* coarse-grid correction: 0 the paper's piecewise-constant
-                        prolongation (Prolong); 1 trilinear cell-centred weights from
-                        the 8 nearest coarse phi1 cells (0) */
+  int prolong;       /* coarse-grid correction into the phi1 cells (fine phi2 cells get
+                        none; the LU-correction that follows sets them), from every
+                        coarse unknown: 1 cell-centred trilinear interpolation (3/4 and
+                        1/4 per axis over the 8 nearest coarse cells, renormalised over
+                        those that are coarse unknowns); 0 the paper's patch-wise
+                        constant Prolong.  With 0 the V-cycle's factor grows with the
+                        number of levels even in the box without shapes (1) */
   int restriction;   /* residual restriction: 0 the paper's 2^-3 sum over the phi1
                         children (Restrict); 1 full weighting, the transpose of the
                         trilinear prolongation over 4 x 4 x 4 fine cells / 8 (0) */
@@ -107,6 +112,13 @@ typedef struct {
                         updates phi with them (no extra V-cycle per restart, and exact
                         for an FP32 V-cycle that is not quite a fixed linear map);
                         0: GMRES that applies the V-cycle again to the combined basis (1) */
+  int fmg;           /* start of the solve: 0 the guess passed in phi (Alg. Multigrid; Sec. 6.3
+                        uses a zero guess); k > 0 Alg. FMG (Sec. 5.4), which replaces the
+                        guess: the data restricted down the hierarchy, the bottom level
+                        solved directly, and on every coarser level the solution of the
+                        level below prolongated into all unknowns and improved by k
+                        V-cycles; the finest level starts from the prolongated solution
+                        and the solve's V-cycles follow (stats count those only) (0) */
 } cc_params;
 
 typedef struct {
@@ -170,7 +182,9 @@ cc_status cc_cut_nodes(const cc_solver* s, int32_t* cells, int64_t* ptr, double*
 cc_status cc_patch_nodes(const cc_solver* s, int32_t* owners, int64_t* ptr, double* xyz, double* w, double* normal);
 /* The phi2 rows of a level (host arrays): cells[n_phi2]; CSR ptr[n_phi2+1],
  * cols[nnz] (grid indices), vals[nnz] (entries of L); boundary terms bptr,
- * bpatch (patch number, finest level only), bcoef (coefficient of <<g>>). */
+ * bpatch (patch number, finest level only; a box-face term of a row next to the
+ * box is coded -(1 + face id), face ids as for g_box), bcoef (coefficient of
+ * <<g>>, or of the box face's <g>). */
 cc_status cc_phi2_rows(const cc_solver* s, int level, int32_t* cells, int32_t* ptr, int32_t* cols, double* vals,
                        int32_t* bptr, int32_t* bpatch, double* bcoef);
 
@@ -241,13 +255,17 @@ cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* r
  *     calls that overlap on the GPU (other streams, other host threads) race
  *     and give wrong results; serialise them.  Nothing in the array has to
  *     start at zero: each call writes what it reads.
+ *   - with the default per-height schedule (lu_schedule = 0) the call only
+ *     enqueues work on the solver's stream and returns without waiting; with
+ *     lu_schedule = 1 it reads the grid barrier's time-out flag, which
+ *     synchronises the solver's stream;
  *   - results agree with cc_lu_correction to rounding (both add partial dot
  *     products with atomics, in an order that varies from call to call). */
 cc_status cc_lu_correction_static(cc_solver* s, int level, double* phi, const double* rhs);
 /* Restrict: coarse[I] = 2^-3 sum of (rhs - L phi) over the phi1 children of I. */
 cc_status cc_restrict_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* coarse);
-/* Prolong: phi1 cells of `level` += coarse value of the parent, where the
- * parent is a phi1 cell of level+1 (coarse phi2 cells prolongate nothing). */
+/* Prolong: phi1 cells of `level` += the coarse correction of level+1 interpolated
+ * by params.prolong (trilinear, or the parent's value), from every coarse unknown. */
 cc_status cc_prolong_add(cc_solver* s, int level, const double* coarse, double* phi);
 /* Bottom solver: phi = L^(M)^{-1} rhs on the coarsest level. */
 cc_status cc_bottom_solve(cc_solver* s, const double* rhs, double* phi);

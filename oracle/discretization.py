@@ -22,7 +22,9 @@ Readings where the paper is silent:
   within 1e-12 h^2 of the largest count as ties, which go to the lowest
   linear index; MAP-3 for all small cells
   first (targets: theta-proper cells), then the BFS of Alg. CellMerging for any
-  cell still below theta.  Cells are treated as single-component.
+  cell still below theta; a grown cell's unknown sits at its largest member
+  (a tip of fluid poking into a cell through an edge otherwise became the
+  owner, with no lattice around it).  Cells are treated as single-component.
 * phi1 needs every in-box cell of {i, i±e^d, i±2e^d} to be a full cell that
   takes part in no merge.
 * The PLG back-tracking of [PLG] is not in the paper.  Feasible lattices are
@@ -32,9 +34,11 @@ Readings where the paper is silent:
   rho = sum_{j != q} |c_j| / |c_q| <= 8 wins; if none of the first 64
   rank-sufficient fits does, the one with the smallest rho (rows with a large
   rho gave the operator spurious low-energy modes on a few cells).  A cell
-  without a degree-4 lattice is merged into a neighbour (up to 4 rounds).  On
-  coarse levels only, degrees 3 and 2 are then tried, and cells still without
-  a lattice are dropped from the coarse problem.
+  without a degree-4 lattice is merged into a neighbour (up to 4 rounds);
+  degrees 3 and 2 are then tried (a cusp of fluid between two barely
+  overlapping shapes has no degree-4 lattice at any resolution); on coarse
+  levels only, cells still without a lattice are dropped from the coarse
+  problem.
 * WLS weights 1 / (1 + |c_k - c_i|^2 / h^2)^2 with c the centroids; one boundary
   row per lattice cell that carries a boundary patch, and one per box face of a
   plain full lattice cell that lies on the box (the walls are boundary too, so
@@ -261,10 +265,12 @@ class Level:
             self._merged_moments()
             self._split()
             failed = self._rows((4,))
-        if failed and coarse:
-            # coarse levels: degree 3, then 2; then cells still without a lattice
-            # are dropped from the coarse problem (zero correction there)
+        if failed:
+            # degree 3, then 2 (a cusp of fluid between two barely overlapping
+            # shapes); on coarse levels cells still without a lattice are then
+            # dropped from the coarse problem (zero correction there)
             failed = self._rows((4, 3, 2))
+        if failed and coarse:
             for _ in range(32):
                 if not failed:
                     break
@@ -344,6 +350,12 @@ class Level:
                             break
             if gvol[i] < theta:
                 raise RuntimeError("cell merging failed: isolated small cells")
+            # the grown cell's unknown sits at its largest member (ties: lowest index)
+            members = np.nonzero(owner == i)[0]
+            best = int(members[np.lexsort((members, -self.vol[members]))[0]])
+            if best != i:
+                owner[members] = best
+                gvol[best] = gvol.pop(i)
         self.owner = owner
         self.slot = (self.kind != 0) & (owner == np.arange(N))
 

@@ -433,12 +433,12 @@ __global__ void k_restrict_fw(const T* __restrict__ r, T* __restrict__ coarse, i
 // cells of the coarse level (a coarse phi2 cell prolongates no correction).
 template <class T>
 __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
-                          const uint8_t* __restrict__ typ_c, int n) {
+                          const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
   const int nc = n / 2;
   const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
   if (k >= n) return;
   const int idx = (i * n + j) * n + k;
-  if (typ[idx] != 1) return;
+  if (typ[idx] != 1 && !(into_phi2 && typ[idx] == 2)) return;
   const int I = ((i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
   if (typ_c[I] != 0) phi[idx] += coarse[I];
 }
@@ -449,12 +449,12 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
 // renormalising the weights over those (so constants are prolongated exactly).
 template <class T>
 __global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
-                              const uint8_t* __restrict__ typ_c, int n) {
+                              const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
   const int nc = n / 2;
   const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
   if (k >= n) return;
   const int idx = (i * n + j) * n + k;
-  if (typ[idx] != 1) return;
+  if (typ[idx] != 1 && !(into_phi2 && typ[idx] == 2)) return;
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1, dk = (k & 1) ? 1 : -1;
   T acc = T(0), wsum = T(0);
@@ -891,6 +891,7 @@ struct DevLevel {
   DevLU lu;
   double *s = nullptr, *e = nullptr, *tmp = nullptr;
   float *s32 = nullptr, *e32 = nullptr, *tmp32 = nullptr;  // mixed precision V-cycle
+  double *fr = nullptr, *fphi = nullptr;  // Alg. FMG: this level's data and solution (levels >= 1)
   dim3 jblock = dim3(16, 8);  // SMO-1 tile (pairs along k x rows along j), tuned at set-up
   template <class T> T* bs();
   template <class T> T* be();
@@ -1456,16 +1457,17 @@ void restrict_resid(cc_solver* S, DevLevel& L, const T* phi, const T* s, T* coar
 }
 
 template <class T>
-void prolong(cc_solver* S, int m, const T* coarse, T* phi) {
+void prolong(cc_solver* S, int m, const T* coarse, T* phi, int into_phi2 = 0) {
   DevLevel& L = S->lev[m];
   const int block = 256;
   ProfScope ps(S, P_PROLONG, (2.0 * sizeof(T) + 1.0 + (sizeof(T) + 1.0) / 8.0) * L.N);
   (void)block;
   if (S->prm.prolong == 1)
     k_prolong_tri<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ,
-                                                                             L.n);
+                                                                             L.n, into_phi2);
   else
-    k_prolong<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n);
+    k_prolong<T><<<grid3(L.n, block3(L.n)), block3(L.n), 0, S->stream>>>(coarse, phi, L.typ, S->lev[m + 1].typ, L.n,
+                                                                         into_phi2);
 }
 
 template <class T>
@@ -1496,18 +1498,57 @@ void vcycle_rec(cc_solver* S, int m, const T* s, T* e) {
   if (cur != e) cudaMemcpyAsync(e, cur, L.N * sizeof(T), cudaMemcpyDeviceToDevice, S->stream);
 }
 
-// e (FP64, level 0) = VCycle(s) in the solver's precision: FP64, or FP32 for the
-// grid work (mixed precision; with precision 2 the LU-corrections too)
-void precond(cc_solver* S, const double* s, double* e) {
-  DevLevel& L = S->lev[0];
+// e (FP64, level m) = VCycle(s) on level m in the solver's precision: FP64, or
+// FP32 for the grid work (mixed precision; with precision 2 the LU-corrections too)
+void precond_level(cc_solver* S, int m, const double* s, double* e) {
+  DevLevel& L = S->lev[m];
   if (S->prm.precision >= 1) {
     k_to_float<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(L.s32, s, L.N);
-    vcycle_rec<float>(S, 0, L.s32, L.e32);
+    vcycle_rec<float>(S, m, L.s32, L.e32);
     cudaMemsetAsync(e, 0, L.N * sizeof(double), S->stream);
     k_axpy_f<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(e, L.e32, L.N);
   } else {
-    vcycle_rec<double>(S, 0, s, e);
+    vcycle_rec<double>(S, m, s, e);
   }
+}
+
+void precond(cc_solver* S, const double* s, double* e) { precond_level(S, 0, s, e); }
+
+// Alg. FMG as the start of the solve (params.fmg V-cycles per level): the data r
+// are restricted down the hierarchy (the Restrict of a zero guess's residual),
+// L^(M) phi = r^(M) is solved by the bottom LU, and on each level m = M-1..1 the
+// solution of level m+1 is prolongated into every unknown (phi1 and phi2) and
+// improved by params.fmg V-cycles on level m's own data; level 0 receives the
+// prolongated level-1 solution, and the V-cycles of the solve follow on it.
+void fmg_start(cc_solver* S) {
+  const int M = (int)S->lev.size() - 1;
+  DevLevel& L0 = S->lev[0];
+  const size_t b0 = L0.N * sizeof(double);
+  if (M == 0) {
+    cudaMemsetAsync(S->phi, 0, b0, S->stream);
+    lu_solve<double>(S, L0.lu, S->r, S->phi);
+    return;
+  }
+  for (int m = 0; m < M; ++m) {
+    DevLevel& L = S->lev[m];
+    cudaMemsetAsync(L.e, 0, L.N * sizeof(double), S->stream);
+    restrict_resid<double>(S, L, L.e, m == 0 ? S->r : L.fr, S->lev[m + 1].fr, L.tmp);
+  }
+  DevLevel& B = S->lev[M];
+  cudaMemsetAsync(B.fphi, 0, B.N * sizeof(double), S->stream);
+  lu_solve<double>(S, B.lu, B.fr, B.fphi);
+  for (int m = M - 1; m >= 1; --m) {
+    DevLevel& L = S->lev[m];
+    cudaMemsetAsync(L.fphi, 0, L.N * sizeof(double), S->stream);
+    prolong<double>(S, m, S->lev[m + 1].fphi, L.fphi, 1);
+    for (int k = 0; k < S->prm.fmg; ++k) {
+      resid(S, L, L.fphi, L.fr, L.s, true, nullptr);
+      precond_level(S, m, L.s, L.e);
+      k_axpy<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(L.fphi, L.e, L.N);
+    }
+  }
+  cudaMemsetAsync(S->phi, 0, b0, S->stream);
+  prolong<double>(S, 0, S->lev[1].fphi, S->phi, 1);
 }
 
 // s0 = r - L phi (all rows) and ||s0||^2 into S->norm
@@ -1622,6 +1663,7 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   CK(cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   const double rn = std::sqrt(*S->hnorm);
+  if (S->prm.fmg > 0) fmg_start(S);
   outer_residual(S);
   CK(cudaStreamSynchronize(S->stream));
   cc_status result = CC_ERR_NOT_CONVERGED;
@@ -1745,6 +1787,7 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   CK(cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   const double rn = std::sqrt(*S->hnorm);
+  if (S->prm.fmg > 0) fmg_start(S);
   cc_status result = CC_ERR_NOT_CONVERGED;
   int cycles = 0, hist_n = 0;
   double rel = 0;
@@ -1943,6 +1986,7 @@ void cc_default_params(cc_params* p) {
   p->prolong = 1;
   p->restriction = 0;
   p->krylov_flexible = 1;
+  p->fmg = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -1993,7 +2037,8 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
       S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
-      S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1) {
+      S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1 ||
+      S->prm.fmg < 0) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }
@@ -2142,6 +2187,10 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dalloc(S, &D.s, D.N));
     TRY(dalloc(S, &D.e, D.N));
     TRY(dalloc(S, &D.tmp, D.N));
+    if (m >= 1) {
+      TRY(dalloc(S, &D.fr, D.N));
+      TRY(dalloc(S, &D.fphi, D.N));
+    }
     if (S->prm.precision >= 1) {
       TRY(dalloc(S, &D.s32, D.N));
       TRY(dalloc(S, &D.e32, D.N));
@@ -2575,8 +2624,12 @@ cc_status cc_lu_correction_static(cc_solver* S, int level, double* phi, const do
       lu_solve_ws<double, double>(S, D, rhs, phi, w, w + (size_t)kStaticLuRows);
     }
     const cudaError_t e = cudaGetLastError();
+    // only the cooperative one-launch sweep (lu_schedule = 1) can raise the
+    // barrier flag; reading it synchronises the stream, so the per-height
+    // schedule skips the read and the call returns without waiting
+    const bool coop_ran = D.coop_grid > 0 && !D.coop_failed;
     if (e != cudaSuccess) st = fail(S, CC_ERR_CUDA, std::string("cc_lu_correction_static: ") + cudaGetErrorString(e));
-    else if (take_timeout(S)) st = fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
+    else if (coop_ran && take_timeout(S)) st = fail(S, CC_ERR_TIMEOUT, "a grid barrier of the LU sweeps waited too long");
   }
   if (prev != S->device) cudaSetDevice(prev);
   return st;

@@ -4,7 +4,8 @@
 //    |C| < theta h^3 into the theta-proper face neighbour with the largest
 //    common (fluid) face (faces within 1e-12 h^2 of the largest tie), ties to
 //    the lowest index; any cell still below theta
-//    grows by breadth-first search.  theta = 0.02.
+//    grows by breadth-first search, and the grown cell's unknown sits at its
+//    largest member.  theta = 0.02.
 //  * The phi1/phi2 split (Sec. 2.3-2.4): phi1 iff every in-box cell of
 //    {i, i±e^d, i±2e^d} is a full cell taking part in no merge.
 //  * eq. regularLaplaceDiscretization with the box ghosts of Sec. 2.3 eliminated
@@ -12,7 +13,7 @@
 //  * FV-PLG (Sec. 4.1): triangular lattices T_4^3 of feasible cells in a fixed
 //    preference order of per-axis coordinate orderings; the first whose fitted
 //    row has rho = sum_{j != q} |c_j| / |c_q| <= 8 wins, else the smallest rho
-//    among the first 64 fits; on coarse levels a cell without one falls back to
+//    among the first 64 fits; a cell without one (after merging) falls back to
 //    degree 3, then 2.
 //  * The weighted least-squares fit in Pi_p^3 (Sec. 2.3): rows are cell averages
 //    of the lattice cells, one boundary row per lattice cell with a patch, and
@@ -386,6 +387,21 @@ struct LevelBuilder {
       if (gv[i] < kTheta) {
         if (err) *err = "cell merging failed: isolated small cells";
         return 2;
+      }
+      // the merged cell's unknown sits at its largest member (ties: lowest
+      // index), not at the small cell the search started from
+      int best = i;
+      double bv = g.vol[i];
+      for (long long y = 0; y < N; ++y)
+        if (L.owner[y] == i && (g.vol[y] > bv || (g.vol[y] == bv && y < best))) {
+          best = (int)y;
+          bv = g.vol[y];
+        }
+      if (best != i) {
+        for (long long y = 0; y < N; ++y)
+          if (L.owner[y] == i) L.owner[y] = best;
+        gv[best] = gv[i];
+        gv.erase(i);
       }
     }
     slot.assign(N, 0);
@@ -869,7 +885,9 @@ int build_level(Level& lv, int n, const std::vector<Ellipsoid>& shapes, int shap
     b.split();
     rc = b.rows(err);
   }
-  if (rc == 1 && coarse) {  // coarse levels: degree 3, then 2
+  // A cell still without a degree-4 lattice (a cusp of fluid between two barely
+  // overlapping shapes) falls back to degree 3, then 2, on every level.
+  if (rc == 1) {
     b.max_degrees = 3;
     rc = b.rows(err);
   }

@@ -278,3 +278,32 @@ def test_solve_host_buffers(pair):
     phi_d = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
     st2, _ = S.solve(dev(f), dev(gb), dev(gp), phi_d)
     assert np.abs(phi - phi_d.cpu().numpy()).max() < 1e-12 * np.abs(phi).max()
+
+
+def test_fmg_parity(pair):
+    """Alg. FMG (Sec. 5.4) as the start of the solve, one V-cycle per level:
+    with max_iter = 1 the library stops after the first V-cycle on level 0, which
+    is the oracle's Alg. FMG with one V-cycle per level."""
+    S, H, (f, gb, gp), r_or, prob = pair
+    K = solver(prob, fmg=1, max_iter=1)
+    lv = H.levels[0]
+    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    K.close()
+    assert st.iters == 1
+    ref = H.fmg(r_or, n_vcycles=1)
+    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-10
+
+
+def test_fmg_start_saves_vcycles(pair):
+    """From the FMG start the solve reaches 1e-10 in fewer V-cycles on level 0."""
+    S, H, (f, gb, gp), r_or, prob = pair
+    K = solver(prob, fmg=1)
+    lv = H.levels[0]
+    phi = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
+    st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    K.close()
+    assert rc == 0 and st.rel_resid < 1e-10
+    ref, hist, it = H.multigrid(r_or, eps=1e-10)
+    assert st.iters < it
+    assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-7

@@ -311,7 +311,19 @@ def _solve_all(solvers, inputs, phis):
 
 
 def _exact_averages(ccmg, W, S):
-    return ccmg.cell_averages_terms(S, W.phi_terms())
+    """Exact cell averages of the manufactured phi on the unknowns' cells: a
+    merged cell's value is the volume-weighted mean over its members (as the
+    discrete unknown is); 0 on cells that are not unknowns."""
+    ex = ccmg.cell_averages_terms(S, W.phi_terms())
+    kind, typ, owner, vol = S.cell_map(0)
+    live = owner >= 0
+    own = np.where(live, owner, 0)
+    num = np.bincount(own[live], weights=(vol * ex)[live], minlength=len(ex))
+    den = np.bincount(own[live], weights=vol[live], minlength=len(ex))
+    out = np.zeros_like(ex)
+    u = typ > 0
+    out[u] = num[u] / den[u]
+    return out
 
 
 def run_ours(args):
@@ -497,12 +509,13 @@ def run_extras(args, ccmg, W, torch, stream, probs, inputs, phi_head, head_stats
     variants on the first seed, and the convergence order of the first seed."""
     n = args.n
     local = torch.cuda.current_device()
-    phi = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
 
     def solve_with(prob, x, **over):
-        S = ccmg.Solver(n if over.get("_n") is None else over["_n"], prob.shapes, prob.shape_bc, prob.box_bc,
+        nn = n if over.get("_n") is None else over["_n"]
+        S = ccmg.Solver(nn, prob.shapes, prob.shape_bc, prob.box_bc,
                         device=local, **{k: v for k, v in dict(kw, **over).items() if k != "_n"})
         S.set_stream(stream)
+        phi = torch.zeros(nn ** 3, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
             for _ in range(2):  # the second solve is the measured one
                 phi.zero_()

@@ -216,6 +216,24 @@ cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, co
 /* The same iteration for an already assembled r (grid array). */
 cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_stats* stats);
 
+/* Learned initial guess (include/ccnet.h; no counterpart in the paper, whose
+ * solve follows it unchanged).  cc_guess_inputs writes the network's input for
+ * the data (f, g_box, g_patch as for cc_solve) into inputs [n^3][3] FP32 (host
+ * or device per `where`): f / s on the unknowns, the fluid volume fraction of
+ * each cell, and the boundary data / s (a cell's patch average, else the mean
+ * of the box-face averages of its faces on the box, else 0), with the data
+ * scale s = RMS of f over the unknowns (1 if f vanishes) returned in *scale;
+ * the solution of the data divided by s is the network's target.
+ * cc_solve_learned runs the network on those inputs (its grid must hold the
+ * solver's finest n), starts the solve from s times its output, and then
+ * iterates exactly as cc_solve (stats count the V-cycles after the guess;
+ * ms_solve excludes the network). */
+typedef struct ccnet ccnet;
+cc_status cc_guess_inputs(cc_solver* s, const double* f, const double* g_box, const double* g_patch, float* inputs,
+                          int where, double* scale);
+cc_status cc_solve_learned(cc_solver* s, ccnet* net, const double* f, const double* g_box, const double* g_patch,
+                           double* phi, int where, cc_stats* stats);
+
 /* ---- hot-path steps, device pointers, grid arrays of `level`, FP64 ------- */
 /* out = s - L phi on phi1 rows (and on phi2 rows if phi2_rows != 0, else 0). */
 cc_status cc_residual(cc_solver* s, int level, const double* phi, const double* rhs, double* out, int phi2_rows);

@@ -12,7 +12,7 @@
  * levels; decoder levels l = 2..0: nearest-neighbour upsampling by 2 of level
  * l+1, concatenation with the encoder's level-l output, two 3x3x3
  * convolutions with ReLU; a 1x1x1 convolution to one output channel (FP32, no
- * activation).  1 460 129 parameters counted without the padded input
+ * activation).  1 460 449 parameters counted without the padded input
  * channels.  Grids n^3 with n a multiple of 8.
  *
  * Layouts.  Activations are NDHWC: a grid of n^3 cells (index (i*n + j)*n + k,
@@ -34,13 +34,13 @@
 extern "C" {
 #endif
 
-typedef struct ccnet ccnet;
+/* struct ccnet is declared in ccmg.h */
 
 /* One 3x3x3 convolution layer on the tensor cores (building block, tested on
  * its own against a CPU direct convolution):
  *   y[v][co] = act(b[co] + sum_t sum_ci w[co][t][ci] * x[v + off(t)][ci])
  * over an n^3 grid with zero padding; x has cin channels, y cout.  cin and
- * cout are multiples of 16 with cin <= 256 and cout <= 128.  relu != 0 applies
+ * cout are multiples of 16 with cin <= 256 and cout <= 256.  relu != 0 applies
  * max(0, .).  b may be NULL (no bias).  y_bf16 receives BF16 output, y_f32 (may
  * be NULL) also the FP32 value before rounding.  Errors: CC_ERR_INVALID_ARG
  * for bad sizes or NULL x/w/y_bf16; CC_ERR_TIMEOUT if a bounded wait on the
@@ -54,7 +54,8 @@ cc_status ccnet_conv3d(int device, int n, int cin, int cout, const uint16_t* x, 
  *   dw[co][t][ci] += sum_v g[v][co] * x[v + off(t)][ci]         (FP32, accumulated)
  *   db[co] += sum_v g[v][co]                                   (FP32, may be NULL)
  * dx runs on the tensor cores as a convolution with the taps mirrored and the
- * channel roles swapped; dw as a GEMM over the grid (K = n^3) per tap. */
+ * channel roles swapped; dw as a GEMM over the grid (K = n^3) per tap, whose
+ * 128-row tile holds cout <= 128 (CC_ERR_INVALID_ARG otherwise). */
 cc_status ccnet_conv3d_backward(int device, int n, int cin, int cout, const uint16_t* x, const uint16_t* w,
                                 const uint16_t* g, float* dx, float* dw, float* db, void* stream);
 

@@ -100,9 +100,15 @@ def init_params(seed=0):
     return P
 
 
-def forward(P, inp):
+def _same(a):
+    return a
+
+
+def forward(P, inp, rnd=_same):
     """U-Net forward (the network of include/ccnet.h) on an (n, n, n, 3) input;
-    returns the (n, n, n) output and the cache of every layer's input and output."""
+    returns the (n, n, n) output and the cache of every layer's input and output.
+    ``rnd`` is applied to every stored activation (``bf16`` reproduces the BF16
+    storage of the tensor-core path; the default keeps FP64)."""
     cache = []
     h = inp
     skips = []
@@ -110,18 +116,18 @@ def forward(P, inp):
     for lev in range(4):
         for _ in range(2):
             w, b = P[k]
-            y = conv3d(h, w, b, relu=True)
+            y = rnd(conv3d(h, w, b, relu=True))
             cache.append((h, y))
             h = y
             k += 1
         skips.append(h)
         if lev < 3:
-            h = avgpool(h)
+            h = rnd(avgpool(h))
     for lev in (2, 1, 0):
         h = np.concatenate([skips[lev], upsample(h)], axis=-1)
         for _ in range(2):
             w, b = P[k]
-            y = conv3d(h, w, b, relu=True)
+            y = rnd(conv3d(h, w, b, relu=True))
             cache.append((h, y))
             h = y
             k += 1
@@ -131,8 +137,10 @@ def forward(P, inp):
     return out, cache
 
 
-def backward(P, cache, dout):
-    """Gradients of sum(dout * forward(P, inp)) with respect to every parameter."""
+def backward(P, cache, dout, rnd=_same):
+    """Gradients of sum(dout * forward(P, inp)) with respect to every parameter;
+    ``rnd`` is applied to each layer's output gradient after the ReLU derivative
+    (the BF16 operand of the tensor-core backward)."""
     grads = [None] * len(P)
     k = len(P) - 1
     h, _ = cache[k]
@@ -144,7 +152,7 @@ def backward(P, cache, dout):
     for lev in (0, 1, 2):
         for _ in range(2):
             x, y = cache[k]
-            g = dh * (y > 0)
+            g = rnd(dh * (y > 0))
             dx, dw, db = conv3d_backward(x, P[k][0], g)
             grads[k] = (dw, db)
             dh = dx
@@ -157,7 +165,7 @@ def backward(P, cache, dout):
             dh = dh + skip_grads[lev]
         for _ in range(2):
             x, y = cache[k]
-            g = dh * (y > 0)
+            g = rnd(dh * (y > 0))
             dx, dw, db = conv3d_backward(x, P[k][0], g)
             grads[k] = (dw, db)
             dh = dx

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libccmg.so")
 BUILD = os.path.join(ROOT, "_build")
 
 CXX_SOURCES = ["geometry.cpp", "setup.cpp", "sparse_lu.cpp"]
-CU_SOURCES = ["ccmg.cu"]
+CU_SOURCES = ["ccmg.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,6 +30,7 @@ def _nvcc():
 def _sources_mtime():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(ROOT, "include", "ccmg.h"))
+    files.append(os.path.join(ROOT, "include", "ccnet.h"))
     return max(os.path.getmtime(f) for f in files)
 
 

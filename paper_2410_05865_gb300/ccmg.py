@@ -96,6 +96,8 @@ SIGNATURES = {
     "cc_profile": (C.c_int, [_P, C.c_int]),
     "cc_lu_check": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "cc_profile_entry": (C.c_char_p, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D]),
+    "cc_guess_inputs": (C.c_int, [_P, _P, _P, _P, _P, C.c_int, _D]),
+    "cc_solve_learned": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.POINTER(cc_stats)]),
 }
 
 _lib = None
@@ -259,6 +261,25 @@ class Solver:
         rc = lib().cc_solve_r(self._h, _ptr(r), _ptr(phi), where, C.byref(st))
         if rc not in (0, 6):
             self._check(rc, "cc_solve_r")
+        return st, rc
+
+    def guess_inputs(self, f, g_box, g_patch, out):
+        """The learned guess's input channels for the data (see cc_guess_inputs);
+        returns the data scale s."""
+        where = CC_HOST if isinstance(out, np.ndarray) else CC_DEVICE
+        sc = C.c_double()
+        self._check(lib().cc_guess_inputs(self._h, _ptr(f), _ptr(g_box), _ptr(g_patch), _ptr(out), where,
+                                          C.byref(sc)), "cc_guess_inputs")
+        return sc.value
+
+    def solve_learned(self, net, f, g_box, g_patch, phi):
+        """cc_solve_learned with a ccnet.Net: the network's guess, then the solve."""
+        where = CC_HOST if isinstance(phi, np.ndarray) or not phi.is_cuda else CC_DEVICE
+        st = cc_stats()
+        rc = lib().cc_solve_learned(self._h, net._h, _ptr(f), _ptr(g_box), _ptr(g_patch), _ptr(phi), where,
+                                    C.byref(st))
+        if rc not in (0, 6):
+            self._check(rc, "cc_solve_learned")
         return st, rc
 
     def set_stream(self, stream):

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/ccmg.h"
+#include "../../include/ccnet.h"
 #include "setup.hpp"
 
 using namespace ccmg;
@@ -841,6 +842,56 @@ __global__ void k_patch_terms(int n2, const int* __restrict__ cell, const int* _
   }
 }
 
+// sum of f^2 over the unknowns (the data scale of the learned guess)
+__global__ void k_sumsq_unknowns(const double* __restrict__ f, const uint8_t* __restrict__ typ, long long N,
+                                 double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    if (typ[i]) acc = fma(f[i], f[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// Learned-guess input channels of every finest cell: f / s on unknowns, the
+// fluid volume fraction, and the boundary data / s (the patch average of a
+// cell with a patch, else the mean of the box-face averages of the cell's faces
+// on the box, else 0).
+__global__ void k_guess_inputs(const double* __restrict__ f, const double* __restrict__ gbox,
+                               const double* __restrict__ gpatch, const uint8_t* __restrict__ typ,
+                               const float* __restrict__ vol, const int* __restrict__ cellpatch, int n, double inv_s,
+                               float* __restrict__ out) {
+  const long long N = (long long)n * n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c[3] = {(int)(idx / ((long long)n * n)), (int)((idx / n) % n), (int)(idx % n)};
+    double g = 0.0;
+    const int p = cellpatch[idx];
+    if (p >= 0) {
+      g = gpatch[p];
+    } else if (vol[idx] > 0.0f) {
+      int cnt = 0;
+      for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side)
+          if (c[d] == (side ? n - 1 : 0)) {
+            const int t0 = d == 0 ? c[1] : c[0], t1 = d == 2 ? c[1] : c[2];
+            g += gbox[((long long)(2 * d + side) * n + t0) * n + t1];
+            ++cnt;
+          }
+      if (cnt) g /= cnt;
+    }
+    out[idx * 3 + 0] = typ[idx] ? (float)(f[idx] * inv_s) : 0.0f;
+    out[idx * 3 + 1] = vol[idx];
+    out[idx * 3 + 2] = (float)(g * inv_s);
+  }
+}
+
+// phi = s * guess on the unknowns, 0 elsewhere
+__global__ void k_apply_guess(const float* __restrict__ gout, double s, const uint8_t* __restrict__ typ, long long N,
+                              double* __restrict__ phi) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    phi[i] = typ[i] ? s * (double)gout[i] : 0.0;
+}
+
 // absorbed cells report their owner's value
 __global__ void k_absorbed(double* __restrict__ phi, int na, const int* __restrict__ cell, const int* __restrict__ own) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < na; q += gridDim.x * blockDim.x) phi[cell[q]] = phi[own[q]];
@@ -938,6 +989,9 @@ struct cc_solver {
   unsigned int* err_flag = nullptr;  // raised by a bounded wait of the one-launch sweeps
   // finest level extras
   double *r = nullptr, *phi = nullptr, *s0 = nullptr, *f = nullptr, *gbox = nullptr, *gpatch = nullptr;
+  float* vol0 = nullptr;      // fluid volume fraction per finest cell (learned-guess input)
+  int* cellpatch = nullptr;   // patch number of each finest cell (-1: none)
+  float *ginp = nullptr, *gout = nullptr;  // learned-guess input [N][3] and output [N], allocated on first use
   double* norm = nullptr;   // device scalar
   double* hnorm = nullptr;  // pinned host scalar
   int ngroups = 0;
@@ -2224,6 +2278,13 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     }
     std::vector<int> patch_of = finish_host_info(S);
     TRY(dalloc(S, &S->gpatch, S->patch_owner.size()));
+    {
+      std::vector<float> v0(L0.geo.vol.begin(), L0.geo.vol.end());
+      std::vector<int> cp(L0.geo.vol.size(), -1);
+      for (size_t q = 0; q < S->patch_owner.size(); ++q) cp[S->patch_owner[q]] = (int)q;
+      TRY(dupload(S, &S->vol0, v0));
+      TRY(dupload(S, &S->cellpatch, cp));
+    }
     std::vector<int> bp(L0.p2_bpatch.size());
     // patch terms index g_patch; box-face terms keep their code -(1 + face id) into g_box
     for (size_t q = 0; q < bp.size(); ++q)
@@ -2420,6 +2481,58 @@ cc_status cc_solve(cc_solver* S, const double* f, const double* g_box, const dou
   CK(cudaMemcpyAsync(S->phi, phi, L.N * sizeof(double),
                      where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
   k_mask<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->phi, L.typ, L.N);
+  return run_solve(S, phi, where, stats);
+}
+
+// data scale s = RMS of f over the unknowns (1 if f vanishes) and the learned-guess inputs in S->ginp
+static cc_status guess_inputs(cc_solver* S, const double* f, const double* g_box, const double* g_patch, int where,
+                              double* scale) {
+  cc_status st = build_rhs(S, f, g_box, g_patch, where);
+  if (st) return st;
+  DevLevel& L = S->lev[0];
+  if (!S->ginp) {
+    if ((st = dalloc(S, &S->ginp, (size_t)L.N * 3)) || (st = dalloc(S, &S->gout, (size_t)L.N))) return st;
+  }
+  CK(cudaMemsetAsync(S->norm, 0, sizeof(double), S->stream));
+  k_sumsq_unknowns<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->f, L.typ, L.N, S->norm);
+  CK(cudaMemcpyAsync(S->hnorm, S->norm, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  const double ms = *S->hnorm / std::max(1, S->info.n_unknowns[0]);
+  const double s = ms > 0.0 ? std::sqrt(ms) : 1.0;
+  k_guess_inputs<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->f, S->gbox, S->gpatch, L.typ, S->vol0, S->cellpatch,
+                                                               L.n, 1.0 / s, S->ginp);
+  CK(cudaGetLastError());
+  *scale = s;
+  return CC_OK;
+}
+
+cc_status cc_guess_inputs(cc_solver* S, const double* f, const double* g_box, const double* g_patch, float* inputs,
+                          int where, double* scale) {
+  if (!S || !inputs || !scale) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  cc_status st = guess_inputs(S, f, g_box, g_patch, where, scale);
+  if (st) return st;
+  const size_t bytes = (size_t)S->lev[0].N * 3 * sizeof(float);
+  CK(cudaMemcpyAsync(inputs, S->ginp, bytes, where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return CC_OK;
+}
+
+cc_status cc_solve_learned(cc_solver* S, ccnet* net, const double* f, const double* g_box, const double* g_patch,
+                           double* phi, int where, cc_stats* stats) {
+  if (!S || !net || !phi) return CC_ERR_INVALID_ARG;
+  if (S->host_only) return fail(S, CC_ERR_INVALID_ARG, "solver was set up host-only (device < 0)");
+  double s = 1.0;
+  cc_status st = guess_inputs(S, f, g_box, g_patch, where, &s);
+  if (st) return st;
+  DevLevel& L = S->lev[0];
+  CK(cudaStreamSynchronize(S->stream));
+  st = ccnet_forward(net, L.n, S->ginp, S->gout, CC_DEVICE);
+  if (st) return fail(S, st, "ccnet_forward failed (the network's grid must be at least the solver's)");
+  CK(cudaSetDevice(S->device));
+  k_apply_guess<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->gout, s, L.typ, L.N, S->phi);
+  CK(cudaGetLastError());
   return run_solve(S, phi, where, stats);
 }
 

@@ -452,7 +452,7 @@ cc_status flag_status(cudaStream_t st) {
 }
 
 bool valid_channels(int cin, int cout) {
-  return cin >= 16 && cin <= 256 && cin % 16 == 0 && cout >= 16 && cout <= 128 && cout % 16 == 0;
+  return cin >= 16 && cin <= 256 && cin % 16 == 0 && cout >= 16 && cout <= 256 && cout % 16 == 0;
 }
 
 }  // namespace ccnet_impl
@@ -489,13 +489,12 @@ cc_status ccnet_conv3d(int device, int n, int cin, int cout, const uint16_t* x, 
 
 cc_status ccnet_conv3d_backward(int device, int n, int cin, int cout, const uint16_t* x, const uint16_t* w,
                                 const uint16_t* g, float* dx, float* dw, float* db, void* stream) {
-  if (n < 1 || !x || !w || !g || !valid_channels(cin, cout) || cout > 256 || cin > 128 + 128) return CC_ERR_INVALID_ARG;
+  if (n < 1 || !x || !w || !g || !valid_channels(cin, cout) || cout > 128) return CC_ERR_INVALID_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return CC_ERR_CUDA;
   if (!g_err && cudaMalloc(&g_err, sizeof(unsigned)) != cudaSuccess) return CC_ERR_OOM;
   cudaStream_t st = (cudaStream_t)stream;
   const long long V = (long long)n * n * n;
   if (dx) {
-    if (cin > 128) return CC_ERR_INVALID_ARG;  // the input-gradient tile holds at most 128 output channels
     __nv_bfloat16* wt = nullptr;
     __nv_bfloat16* scratch = nullptr;
     if (cudaMalloc(&wt, (size_t)cin * 27 * cout * 2) != cudaSuccess) return CC_ERR_OOM;
@@ -539,6 +538,617 @@ cc_status ccnet_conv3d_backward(int device, int n, int cin, int cout, const uint
   if (db) k_bias_grad<<<256, 128, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(g), V, cout, db);
   if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
   return flag_status(st);
+}
+
+}  // extern "C"
+
+namespace ccnet_impl {
+
+// ------------------------------------------------------------ small kernels
+#define GRID_STRIDE(i, N) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (N); \
+                               i += (long long)gridDim.x * blockDim.x)
+
+// input FP32 [V][3] -> BF16 [V][16], channels 3..15 zero
+__global__ void k_input(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long V) {
+  GRID_STRIDE(v, V) {
+    __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = __float2bfloat16_rn(c < 3 ? in[v * 3 + c] : 0.0f);
+    uint4* o = reinterpret_cast<uint4*>(out + v * 16);
+    o[0] = reinterpret_cast<const uint4*>(h)[0];
+    o[1] = reinterpret_cast<const uint4*>(h)[1];
+  }
+}
+
+// 2x2x2 average pooling of channels [col, col + C) of x (edge n, row stride xs) into y [(n/2)^3][C]
+__global__ void k_pool(const __nv_bfloat16* __restrict__ x, int n, int xs, int col, int C,
+                       __nv_bfloat16* __restrict__ y) {
+  const int m = n / 2;
+  const long long total = (long long)m * m * m * C;
+  GRID_STRIDE(e, total) {
+    const int c = (int)(e % C);
+    const long long u = e / C;
+    const int I = (int)(u / ((long long)m * m)), J = (int)((u / m) % m), K = (int)(u % m);
+    float s = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const long long v = ((long long)(2 * I + (d >> 2)) * n + (2 * J + ((d >> 1) & 1))) * n + (2 * K + (d & 1));
+      s += __bfloat162float(x[v * xs + col + c]);
+    }
+    y[u * C + c] = __float2bfloat16_rn(0.125f * s);
+  }
+}
+
+// nearest upsampling: y[v][col + c] = x[parent(v)][c], x [(n/2)^3][C], y edge n, stride ys
+__global__ void k_upsample(const __nv_bfloat16* __restrict__ x, int n, int C, __nv_bfloat16* __restrict__ y, int ys,
+                           int col) {
+  const int m = n / 2;
+  const long long total = (long long)n * n * n * C;
+  GRID_STRIDE(e, total) {
+    const int c = (int)(e % C);
+    const long long v = e / C;
+    const int i = (int)(v / ((long long)n * n)), j = (int)((v / n) % n), k = (int)(v % n);
+    const long long u = ((long long)(i >> 1) * m + (j >> 1)) * m + (k >> 1);
+    y[v * ys + col + c] = x[u * C + c];
+  }
+}
+
+// out[v] = b + sum_c w[c] x[v][c]   (the 1x1x1 output layer, 16 channels)
+__global__ void k_out_fwd(const __nv_bfloat16* __restrict__ x, const float* __restrict__ w, const float* __restrict__ b,
+                          float* __restrict__ out, long long V) {
+  GRID_STRIDE(v, V) {
+    float s = b[0];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += w[c] * __bfloat162float(x[v * 16 + c]);
+    out[v] = s;
+  }
+}
+
+// weighted squared error: acc[0] += sum w (o - t)^2, acc[1] += sum w
+__global__ void k_loss_sums(const float* __restrict__ o, const float* __restrict__ t, const float* __restrict__ w,
+                            long long V, double* __restrict__ acc) {
+  double a = 0.0, b = 0.0;
+  GRID_STRIDE(v, V) {
+    const double d = (double)o[v] - (double)t[v];
+    a += (double)w[v] * d * d;
+    b += (double)w[v];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+  }
+}
+
+// dout[v] = scale * 2 w (o - t) / sum w
+__global__ void k_loss_grad(const float* __restrict__ o, const float* __restrict__ t, const float* __restrict__ w,
+                            long long V, const double* __restrict__ acc, float scale, float* __restrict__ dout) {
+  const double inv = acc[1] > 0.0 ? 1.0 / acc[1] : 0.0;
+  GRID_STRIDE(v, V) dout[v] = (float)(scale * 2.0 * (double)w[v] * ((double)o[v] - (double)t[v]) * inv);
+}
+
+// output layer backward: gw[c] += sum_v dout x[v][c], gb += sum dout,
+// g[v][c] = bf16(dout[v] w[c] * (x[v][c] > 0))  (x is the ReLU output of the layer before)
+__global__ void k_out_bwd(const __nv_bfloat16* __restrict__ x, const float* __restrict__ w,
+                          const float* __restrict__ dout, long long V, float* __restrict__ gw, float* __restrict__ gb,
+                          __nv_bfloat16* __restrict__ g) {
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+  float ab = 0.0f;
+  GRID_STRIDE(v, V) {
+    const float d = dout[v];
+    ab += d;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float xv = __bfloat162float(x[v * 16 + c]);
+      acc[c] += d * xv;
+      g[v * 16 + c] = __float2bfloat16_rn(xv > 0.0f ? d * w[c] : 0.0f);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float s = acc[c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(gw + c, s);
+  }
+  for (int off = 16; off > 0; off >>= 1) ab += __shfl_down_sync(0xffffffffu, ab, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(gb, ab);
+}
+
+// g[v][c] = bf16((a[v][aoff + c] (+ b[v][c])) * (y[v][ycol + c] > 0)), c < C
+__global__ void k_mask(const float* __restrict__ a, int as, int aoff, const float* __restrict__ b,
+                       const __nv_bfloat16* __restrict__ y, int ys, int ycol, long long V, int C,
+                       __nv_bfloat16* __restrict__ g) {
+  GRID_STRIDE(e, V * C) {
+    const int c = (int)(e % C);
+    const long long v = e / C;
+    float s = a[v * as + aoff + c];
+    if (b) s += b[v * C + c];
+    g[v * C + c] = __float2bfloat16_rn(__bfloat162float(y[v * ys + ycol + c]) > 0.0f ? s : 0.0f);
+  }
+}
+
+// coarse[u][c] = sum of the 8 children of dx[v][off + c] (backward of nearest upsampling)
+__global__ void k_upsample_bwd(const float* __restrict__ dx, int n, int xs, int off, int C, float* __restrict__ coarse) {
+  const int m = n / 2;
+  GRID_STRIDE(e, (long long)m * m * m * C) {
+    const int c = (int)(e % C);
+    const long long u = e / C;
+    const int I = (int)(u / ((long long)m * m)), J = (int)((u / m) % m), K = (int)(u % m);
+    float s = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const long long v = ((long long)(2 * I + (d >> 2)) * n + (2 * J + ((d >> 1) & 1))) * n + (2 * K + (d & 1));
+      s += dx[v * xs + off + c];
+    }
+    coarse[u * C + c] = s;
+  }
+}
+
+// fine[v][c] += coarse[parent(v)][c] / 8 (backward of average pooling)
+__global__ void k_pool_bwd(const float* __restrict__ coarse, int n, int C, float* __restrict__ fine) {
+  const int m = n / 2;
+  GRID_STRIDE(e, (long long)n * n * n * C) {
+    const int c = (int)(e % C);
+    const long long v = e / C;
+    const int i = (int)(v / ((long long)n * n)), j = (int)((v / n) % n), k = (int)(v % n);
+    fine[v * C + c] += 0.125f * coarse[(((long long)(i >> 1) * m + (j >> 1)) * m + (k >> 1)) * C + c];
+  }
+}
+
+// master FP32 weights [cout][taps][cin_real] -> BF16 [cout][taps][cin_store] (zero padded)
+// and the mirrored copy [cin_store][27][cout] of the input-gradient convolution
+__global__ void k_pack(const float* __restrict__ mw, int cout, int taps, int cin_real, int cin_store,
+                       __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt) {
+  GRID_STRIDE(e, (long long)cout * taps * cin_store) {
+    const int ci = (int)(e % cin_store), t = (int)((e / cin_store) % taps), co = (int)(e / ((long long)cin_store * taps));
+    const float val = ci < cin_real ? mw[((long long)co * taps + t) * cin_real + ci] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(val);
+    w[e] = h;
+    if (wt && taps == 27) wt[((long long)ci * 27 + (26 - t)) * cout + co] = h;
+  }
+}
+
+// gradient [cout][27][cin_store] FP32 -> master layout [cout][27][cin_real] (+=)
+__global__ void k_unpack_grad(const float* __restrict__ gs, int cout, int cin_real, int cin_store,
+                              float* __restrict__ gm) {
+  GRID_STRIDE(e, (long long)cout * 27 * cin_real) {
+    const int ci = (int)(e % cin_real);
+    const long long rest = e / cin_real;  // co * 27 + t
+    gm[e] += gs[rest * cin_store + ci];
+  }
+}
+
+// Adam on the FP32 master parameters (bias-corrected step sizes given)
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long N, float lr_t, float b1, float b2, float eps) {
+  GRID_STRIDE(i, N) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr_t * mi / (sqrtf(vi) + eps);
+  }
+}
+
+}  // namespace ccnet_impl
+
+// ---------------------------------------------------------------- the network
+struct ccnet {
+  int device = 0;
+  int n_max = 0;
+  cudaStream_t stream = nullptr;
+  struct Layer {
+    int cin_real, cin, cout, taps;
+    long long w_off, b_off;             // into the FP32 master parameters
+    __nv_bfloat16* w = nullptr;         // [cout][taps][cin] BF16
+    __nv_bfloat16* wt = nullptr;        // [cin][27][cout] BF16 (input-gradient convolution)
+    float* dws = nullptr;               // [cout][27][cin] FP32 weight gradient (padded layout)
+  };
+  std::vector<Layer> L;
+  long long np = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master params, grads, Adam moments
+  long long step = 0;
+  // activations (edge n_l = n >> l)
+  __nv_bfloat16* in0 = nullptr;
+  __nv_bfloat16 *enc_a[4] = {}, *cat[3] = {}, *pooled[4] = {}, *e3b = nullptr, *dec_a[3] = {}, *dec_b[3] = {};
+  float* out = nullptr;
+  // backward work
+  float *dout = nullptr, *dxa = nullptr, *dxb = nullptr, *dskip[3] = {}, *dcoarse = nullptr;
+  __nv_bfloat16* gbuf = nullptr;
+  double* lacc = nullptr;
+  unsigned* err = nullptr;
+  float *hin = nullptr, *hout = nullptr;  // device staging of host inputs / outputs
+  std::vector<void*> allocs;
+};
+
+namespace ccnet_impl {
+
+constexpr int kCh[4] = {16, 32, 64, 128};
+
+template <class T>
+cc_status nalloc(ccnet* N, T** p, size_t count) {
+  *p = nullptr;
+  if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return CC_ERR_OOM;
+  N->allocs.push_back((void*)*p);
+  return CC_OK;
+}
+
+#define NTRY(x)                 \
+  do {                          \
+    cc_status s_ = (x);         \
+    if (s_ != CC_OK) return s_; \
+  } while (0)
+#define NCK(x)                                    \
+  do {                                            \
+    if ((x) != cudaSuccess) return CC_ERR_CUDA;   \
+  } while (0)
+
+inline unsigned blocks(long long n, int per = 256) {
+  return (unsigned)std::max(1LL, std::min((n + per - 1) / per, 152LL * 16));
+}
+
+cc_status conv(ccnet* N, int li, int n, const __nv_bfloat16* x, int xstride, __nv_bfloat16* y, int ystride, int ycol,
+               int relu) {
+  const ccnet::Layer& l = N->L[li];
+  ConvFwd p{};
+  p.n = n;
+  p.cin = l.cin;
+  p.cout = l.cout;
+  p.xstride = xstride;
+  p.ystride = ystride;
+  p.ycol = ycol;
+  p.taps = l.taps;
+  p.x = x;
+  p.w = l.w;
+  p.bias = N->p + l.b_off;
+  p.relu = relu;
+  p.y = y;
+  p.yf = nullptr;
+  p.err = N->err;
+  p.tcols = tmem_cols(l.cout);
+  NCK(launch_fwd(p, N->stream));
+  return CC_OK;
+}
+
+// input gradient of layer li into dx (FP32 [V][cin]) and weight/bias gradients,
+// from g (BF16 [V][cout], ReLU derivative applied); x (row stride xs) is the layer's input
+cc_status conv_back(ccnet* N, int li, int n, const __nv_bfloat16* x, int xs, const __nv_bfloat16* g, float* dx) {
+  const ccnet::Layer& l = N->L[li];
+  const long long V = (long long)n * n * n;
+  if (dx) {
+    ConvFwd p{};
+    p.n = n;
+    p.cin = l.cout;
+    p.cout = l.cin;
+    p.xstride = l.cout;
+    p.ystride = l.cin;
+    p.taps = 27;
+    p.x = g;
+    p.w = l.wt;
+    p.y = nullptr;
+    p.yf = dx;
+    p.err = N->err;
+    p.tcols = tmem_cols(l.cin);
+    NCK(launch_fwd(p, N->stream));
+  }
+  NCK(cudaMemsetAsync(l.dws, 0, (size_t)l.cout * 27 * l.cin * sizeof(float), N->stream));
+  ConvWgrad q{};
+  q.n = n;
+  q.cin = l.cin;
+  q.cout = l.cout;
+  q.xstride = xs;
+  q.x = x;
+  q.g = g;
+  q.dw = l.dws;
+  q.err = N->err;
+  q.tcols = tmem_cols(l.cin);
+  NCK(launch_wgrad(q, N->stream, N->device));
+  k_unpack_grad<<<blocks((long long)l.cout * 27 * l.cin_real), 256, 0, N->stream>>>(l.dws, l.cout, l.cin_real, l.cin,
+                                                                                   N->g + l.w_off);
+  k_bias_grad<<<256, 128, 0, N->stream>>>(g, V, l.cout, N->g + l.b_off);
+  NCK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status pack_all(ccnet* N) {
+  for (int i = 0; i < 14; ++i) {  // the 1x1x1 output layer reads its FP32 master weights directly
+    const ccnet::Layer& l = N->L[i];
+    k_pack<<<blocks((long long)l.cout * l.taps * l.cin), 256, 0, N->stream>>>(N->p + l.w_off, l.cout, l.taps,
+                                                                              l.cin_real, l.cin, l.w, l.wt);
+  }
+  NCK(cudaGetLastError());
+  return CC_OK;
+}
+
+// Forward on an n^3 grid from N->in0 (already filled); result in N->out.
+cc_status forward(ccnet* N, int n) {
+  const int n1 = n / 2, n2 = n / 4, n3 = n / 8;
+  const int ns[4] = {n, n1, n2, n3};
+  // encoder
+  NTRY(conv(N, 0, n, N->in0, 16, N->enc_a[0], 16, 0, 1));
+  NTRY(conv(N, 1, n, N->enc_a[0], 16, N->cat[0], 48, 0, 1));
+  for (int l = 1; l < 4; ++l) {
+    const int cp = kCh[l - 1], cs = l - 1 < 3 ? kCh[l - 1] + kCh[l] : 0;
+    const long long Vl = (long long)ns[l] * ns[l] * ns[l];
+    k_pool<<<blocks(Vl * cp), 256, 0, N->stream>>>(N->cat[l - 1], ns[l - 1], cs, 0, cp, N->pooled[l]);
+    NTRY(conv(N, 2 * l, ns[l], N->pooled[l], cp, N->enc_a[l], kCh[l], 0, 1));
+    if (l < 3)
+      NTRY(conv(N, 2 * l + 1, ns[l], N->enc_a[l], kCh[l], N->cat[l], kCh[l] + kCh[l + 1], 0, 1));
+    else
+      NTRY(conv(N, 2 * l + 1, ns[l], N->enc_a[l], kCh[l], N->e3b, kCh[l], 0, 1));
+  }
+  // decoder
+  const __nv_bfloat16* below = N->e3b;
+  for (int l = 2; l >= 0; --l) {
+    const int cs = kCh[l] + kCh[l + 1];
+    const long long Vl = (long long)ns[l] * ns[l] * ns[l];
+    k_upsample<<<blocks(Vl * kCh[l + 1]), 256, 0, N->stream>>>(below, ns[l], kCh[l + 1], N->cat[l], cs, kCh[l]);
+    const int li = 8 + 2 * (2 - l);
+    NTRY(conv(N, li, ns[l], N->cat[l], cs, N->dec_a[l], kCh[l], 0, 1));
+    NTRY(conv(N, li + 1, ns[l], N->dec_a[l], kCh[l], N->dec_b[l], kCh[l], 0, 1));
+    below = N->dec_b[l];
+  }
+  const ccnet::Layer& lo = N->L[14];
+  const long long V = (long long)n * n * n;
+  k_out_fwd<<<blocks(V), 256, 0, N->stream>>>(N->dec_b[0], N->p + lo.w_off, N->p + lo.b_off, N->out, V);
+  NCK(cudaGetLastError());
+  return CC_OK;
+}
+
+// Backward from N->dout (FP32 [V]) through every layer; gradients add into N->g.
+cc_status backward(ccnet* N, int n) {
+  const int ns[4] = {n, n / 2, n / 4, n / 8};
+  const long long V = (long long)n * n * n;
+  const ccnet::Layer& lo = N->L[14];
+  k_out_bwd<<<blocks(V), 256, 0, N->stream>>>(N->dec_b[0], N->p + lo.w_off, N->dout, V, N->g + lo.w_off,
+                                               N->g + lo.b_off, N->gbuf);
+  // decoder levels 0, 1, 2 (gbuf holds the masked gradient of dec_b[l])
+  for (int l = 0; l <= 2; ++l) {
+    const int li = 8 + 2 * (2 - l);
+    const int C = kCh[l], cs = kCh[l] + kCh[l + 1];
+    const long long Vl = (long long)ns[l] * ns[l] * ns[l];
+    NTRY(conv_back(N, li + 1, ns[l], N->dec_a[l], C, N->gbuf, N->dxa));
+    k_mask<<<blocks(Vl * C), 256, 0, N->stream>>>(N->dxa, C, 0, nullptr, N->dec_a[l], C, 0, Vl, C, N->gbuf);
+    NTRY(conv_back(N, li, ns[l], N->cat[l], cs, N->gbuf, N->dxb));
+    // split: skip part kept, upsampled part summed to the level below
+    NCK(cudaMemcpy2DAsync(N->dskip[l], C * sizeof(float), N->dxb, cs * sizeof(float), C * sizeof(float), Vl,
+                          cudaMemcpyDeviceToDevice, N->stream));
+    const long long Vc = Vl / 8;
+    k_upsample_bwd<<<blocks(Vc * kCh[l + 1]), 256, 0, N->stream>>>(N->dxb, ns[l], cs, C, kCh[l + 1], N->dcoarse);
+    // gradient of the layer below's output (dec_b[l+1], or e3b at the bottom), masked
+    const __nv_bfloat16* ybelow = l < 2 ? N->dec_b[l + 1] : N->e3b;
+    k_mask<<<blocks(Vc * kCh[l + 1]), 256, 0, N->stream>>>(N->dcoarse, kCh[l + 1], 0, nullptr, ybelow, kCh[l + 1], 0,
+                                                            Vc, kCh[l + 1], N->gbuf);
+  }
+  // encoder level 3: gbuf = masked gradient of e3b
+  {
+    const int l = 3;
+    const long long Vl = (long long)ns[l] * ns[l] * ns[l];
+    NTRY(conv_back(N, 7, ns[l], N->enc_a[l], kCh[l], N->gbuf, N->dxa));
+    k_mask<<<blocks(Vl * kCh[l]), 256, 0, N->stream>>>(N->dxa, kCh[l], 0, nullptr, N->enc_a[l], kCh[l], 0, Vl, kCh[l],
+                                                       N->gbuf);
+    NTRY(conv_back(N, 6, ns[l], N->pooled[l], kCh[l - 1], N->gbuf, N->dxb));  // dxb: d(pooled[3]) [V3][64]
+  }
+  for (int l = 2; l >= 0; --l) {
+    const int C = kCh[l], cs = kCh[l] + kCh[l + 1];
+    const long long Vl = (long long)ns[l] * ns[l] * ns[l];
+    // d(skip_l) += pool backward of d(pooled[l+1])
+    k_pool_bwd<<<blocks(Vl * C), 256, 0, N->stream>>>(N->dxb, ns[l], C, N->dskip[l]);
+    k_mask<<<blocks(Vl * C), 256, 0, N->stream>>>(N->dskip[l], C, 0, nullptr, N->cat[l], cs, 0, Vl, C, N->gbuf);
+    NTRY(conv_back(N, 2 * l + 1, ns[l], N->enc_a[l], C, N->gbuf, N->dxa));
+    k_mask<<<blocks(Vl * C), 256, 0, N->stream>>>(N->dxa, C, 0, nullptr, N->enc_a[l], C, 0, Vl, C, N->gbuf);
+    if (l > 0)
+      NTRY(conv_back(N, 2 * l, ns[l], N->pooled[l], kCh[l - 1], N->gbuf, N->dxb));
+    else
+      NTRY(conv_back(N, 0, n, N->in0, 16, N->gbuf, nullptr));
+  }
+  NCK(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status take_err(ccnet* N) {
+  unsigned h = 0;
+  NCK(cudaMemcpyAsync(&h, N->err, sizeof(unsigned), cudaMemcpyDeviceToHost, N->stream));
+  NCK(cudaStreamSynchronize(N->stream));
+  if (h) {
+    cudaMemsetAsync(N->err, 0, sizeof(unsigned), N->stream);
+    return CC_ERR_TIMEOUT;
+  }
+  return CC_OK;
+}
+
+}  // namespace ccnet_impl
+
+extern "C" {
+
+cc_status ccnet_create(int device, int n_max, uint64_t seed, ccnet** out) {
+  if (!out || n_max < 8 || n_max % 8 != 0) return CC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return CC_ERR_CUDA;
+  ccnet* N = new ccnet();
+  N->device = device;
+  N->n_max = n_max;
+  auto fail = [&](cc_status st) {
+    ccnet_destroy(N);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&N->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CC_ERR_CUDA);
+  // layers: (C_out, C_in real, C_in stored)
+  const int shapes[14][3] = {{16, 3, 16},  {16, 16, 16}, {32, 16, 16}, {32, 32, 32},  {64, 32, 32},
+                             {64, 64, 64}, {128, 64, 64}, {128, 128, 128}, {64, 192, 192}, {64, 64, 64},
+                             {32, 96, 96}, {32, 32, 32}, {16, 48, 48}, {16, 16, 16}};
+  long long off = 0;
+  for (int i = 0; i < 15; ++i) {
+    ccnet::Layer l{};
+    if (i < 14) {
+      l.cout = shapes[i][0];
+      l.cin_real = shapes[i][1];
+      l.cin = shapes[i][2];
+      l.taps = 27;
+    } else {
+      l.cout = 1;
+      l.cin_real = l.cin = 16;
+      l.taps = 1;
+    }
+    l.w_off = off;
+    off += (long long)l.cout * l.taps * l.cin_real;
+    l.b_off = off;
+    off += l.cout;
+    N->L.push_back(l);
+  }
+  N->np = off;
+  cc_status st;
+  if ((st = nalloc(N, &N->p, N->np)) || (st = nalloc(N, &N->g, N->np)) || (st = nalloc(N, &N->m, N->np)) ||
+      (st = nalloc(N, &N->v, N->np)))
+    return fail(st);
+  for (int i = 0; i < 14; ++i) {
+    ccnet::Layer& l = N->L[i];
+    if ((st = nalloc(N, &l.w, (size_t)l.cout * 27 * l.cin)) || (st = nalloc(N, &l.wt, (size_t)l.cout * 27 * l.cin)) ||
+        (st = nalloc(N, &l.dws, (size_t)l.cout * 27 * l.cin)))
+      return fail(st);
+  }
+  const long long V0 = (long long)n_max * n_max * n_max;
+  long long Vl[4];
+  for (int l = 0; l < 4; ++l) Vl[l] = V0 >> (3 * l);
+  if ((st = nalloc(N, &N->in0, V0 * 16)) || (st = nalloc(N, &N->e3b, Vl[3] * 128)) || (st = nalloc(N, &N->out, V0)) ||
+      (st = nalloc(N, &N->dout, V0)) || (st = nalloc(N, &N->dxa, V0 * 48)) || (st = nalloc(N, &N->dxb, V0 * 48)) ||
+      (st = nalloc(N, &N->dcoarse, V0 * 8)) || (st = nalloc(N, &N->gbuf, V0 * 16)) || (st = nalloc(N, &N->lacc, 2)) ||
+      (st = nalloc(N, &N->err, 1)) || (st = nalloc(N, &N->hin, V0 * 3)) || (st = nalloc(N, &N->hout, V0)))
+    return fail(st);
+  for (int l = 0; l < 4; ++l) {
+    if ((st = nalloc(N, &N->enc_a[l], Vl[l] * kCh[l]))) return fail(st);
+    if (l >= 1 && (st = nalloc(N, &N->pooled[l], Vl[l] * kCh[l - 1]))) return fail(st);
+    if (l < 3) {
+      if ((st = nalloc(N, &N->cat[l], Vl[l] * (kCh[l] + kCh[l + 1]))) || (st = nalloc(N, &N->dec_a[l], Vl[l] * kCh[l])) ||
+          (st = nalloc(N, &N->dec_b[l], Vl[l] * kCh[l])) || (st = nalloc(N, &N->dskip[l], Vl[l] * kCh[l])))
+        return fail(st);
+    }
+  }
+  if (cudaMemset(N->err, 0, sizeof(unsigned)) != cudaSuccess) return fail(CC_ERR_CUDA);
+  if (cudaMemset(N->m, 0, N->np * 4) != cudaSuccess || cudaMemset(N->v, 0, N->np * 4) != cudaSuccess ||
+      cudaMemset(N->g, 0, N->np * 4) != cudaSuccess)
+    return fail(CC_ERR_CUDA);
+  // He-normal initialisation (std sqrt(2 / (27 C_in))), zero biases; output layer std sqrt(1/16)
+  std::vector<float> h(N->np, 0.0f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (int i = 0; i < 15; ++i) {
+    const ccnet::Layer& l = N->L[i];
+    const double sd = i < 14 ? std::sqrt(2.0 / (27.0 * l.cin_real)) : std::sqrt(1.0 / 16.0);
+    for (long long e = 0; e < (long long)l.cout * l.taps * l.cin_real; ++e) h[l.w_off + e] = (float)(sd * nd(rng));
+  }
+  if (cudaMemcpy(N->p, h.data(), N->np * 4, cudaMemcpyHostToDevice) != cudaSuccess) return fail(CC_ERR_CUDA);
+  if ((st = pack_all(N)) != CC_OK) return fail(st);
+  if (cudaStreamSynchronize(N->stream) != cudaSuccess) return fail(CC_ERR_CUDA);
+  *out = N;
+  return CC_OK;
+}
+
+void ccnet_destroy(ccnet* N) {
+  if (!N) return;
+  cudaSetDevice(N->device);
+  if (N->stream) cudaStreamSynchronize(N->stream);
+  for (void* p : N->allocs) cudaFree(p);
+  if (N->stream) cudaStreamDestroy(N->stream);
+  delete N;
+}
+
+cc_status ccnet_num_params(const ccnet* N, long long* count) {
+  if (!N || !count) return CC_ERR_INVALID_ARG;
+  *count = N->np;
+  return CC_OK;
+}
+
+cc_status ccnet_get_params(const ccnet* N, float* host) {
+  if (!N || !host) return CC_ERR_INVALID_ARG;
+  if (cudaSetDevice(N->device) != cudaSuccess || cudaStreamSynchronize(N->stream) != cudaSuccess) return CC_ERR_CUDA;
+  return cudaMemcpy(host, N->p, N->np * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+cc_status ccnet_get_grads(const ccnet* N, float* host) {
+  if (!N || !host) return CC_ERR_INVALID_ARG;
+  if (cudaSetDevice(N->device) != cudaSuccess || cudaStreamSynchronize(N->stream) != cudaSuccess) return CC_ERR_CUDA;
+  return cudaMemcpy(host, N->g, N->np * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+cc_status ccnet_set_params(ccnet* N, const float* host) {
+  if (!N || !host) return CC_ERR_INVALID_ARG;
+  if (cudaSetDevice(N->device) != cudaSuccess) return CC_ERR_CUDA;
+  if (cudaMemcpyAsync(N->p, host, N->np * 4, cudaMemcpyHostToDevice, N->stream) != cudaSuccess) return CC_ERR_CUDA;
+  cc_status st = pack_all(N);
+  if (st) return st;
+  return cudaStreamSynchronize(N->stream) == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+cc_status ccnet_forward(ccnet* N, int n, const float* input, float* out, int where) {
+  if (!N || !input || !out || n < 8 || n % 8 != 0 || n > N->n_max) return CC_ERR_INVALID_ARG;
+  if (cudaSetDevice(N->device) != cudaSuccess) return CC_ERR_CUDA;
+  const long long V = (long long)n * n * n;
+  const float* in = input;
+  if (where == CC_HOST) {
+    NCK(cudaMemcpyAsync(N->hin, input, V * 3 * 4, cudaMemcpyHostToDevice, N->stream));
+    in = N->hin;
+  }
+  k_input<<<blocks(V), 256, 0, N->stream>>>(in, N->in0, V);
+  cc_status st = forward(N, n);
+  if (st) return st;
+  NCK(cudaMemcpyAsync(out, N->out, V * 4, where == CC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                      N->stream));
+  return take_err(N);
+}
+
+cc_status ccnet_loss_grad(ccnet* N, int n, int batch, const float* inputs, const float* targets, const float* weights,
+                          float* loss) {
+  if (!N || !inputs || !targets || !weights || batch < 1 || n < 8 || n % 8 != 0 || n > N->n_max)
+    return CC_ERR_INVALID_ARG;
+  if (cudaSetDevice(N->device) != cudaSuccess) return CC_ERR_CUDA;
+  const long long V = (long long)n * n * n;
+  NCK(cudaMemsetAsync(N->g, 0, N->np * 4, N->stream));
+  double total = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    k_input<<<blocks(V), 256, 0, N->stream>>>(inputs + (long long)b * V * 3, N->in0, V);
+    cc_status st = forward(N, n);
+    if (st) return st;
+    NCK(cudaMemsetAsync(N->lacc, 0, 2 * sizeof(double), N->stream));
+    k_loss_sums<<<blocks(V), 256, 0, N->stream>>>(N->out, targets + (long long)b * V, weights + (long long)b * V, V,
+                                                  N->lacc);
+    k_loss_grad<<<blocks(V), 256, 0, N->stream>>>(N->out, targets + (long long)b * V, weights + (long long)b * V, V,
+                                                  N->lacc, 1.0f / batch, N->dout);
+    // zero the skip-gradient buffers the backward accumulates into
+    for (int l = 0; l < 3; ++l) {
+      const long long Vl = V >> (3 * l);
+      NCK(cudaMemsetAsync(N->dskip[l], 0, Vl * (long long)kCh[l] * 4, N->stream));
+    }
+    st = backward(N, n);
+    if (st) return st;
+    double h[2];
+    NCK(cudaMemcpyAsync(h, N->lacc, sizeof(h), cudaMemcpyDeviceToHost, N->stream));
+    NCK(cudaStreamSynchronize(N->stream));
+    total += h[1] > 0 ? h[0] / h[1] : 0.0;
+  }
+  if (loss) *loss = (float)(total / batch);
+  return take_err(N);
+}
+
+cc_status ccnet_train_step(ccnet* N, int n, int batch, const float* inputs, const float* targets, const float* weights,
+                           float lr, float* loss) {
+  cc_status st = ccnet_loss_grad(N, n, batch, inputs, targets, weights, loss);
+  if (st) return st;
+  N->step += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const double lr_t = lr * std::sqrt(1.0 - std::pow(b2, (double)N->step)) / (1.0 - std::pow(b1, (double)N->step));
+  k_adam<<<blocks(N->np), 256, 0, N->stream>>>(N->p, N->g, N->m, N->v, N->np, (float)lr_t, (float)b1, (float)b2,
+                                               1e-8f);
+  st = pack_all(N);
+  if (st) return st;
+  NCK(cudaStreamSynchronize(N->stream));
+  return CC_OK;
 }
 
 }  // extern "C"

@@ -27,10 +27,10 @@ def ccmg():
     return m
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "ccmg.h")).read()
+def declared_symbols(header="ccmg.h", prefix="cc_"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(cc_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z_0-9]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(ccmg):
@@ -41,6 +41,17 @@ def test_exports_every_declared_symbol(ccmg):
         assert hasattr(L, name), name
     # and the binding wraps each of them with a signature
     assert set(names) == set(ccmg.SIGNATURES)
+
+
+def test_exports_every_network_symbol(ccmg):
+    """include/ccnet.h (the learned guess): every declared call is exported and bound."""
+    from paper_2410_05865_gb300 import ccnet
+    L = ccnet.lib()
+    names = declared_symbols("ccnet.h", "ccnet_")
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(ccnet.SIGNATURES)
 
 
 def test_status_strings(ccmg):

@@ -6,8 +6,10 @@ so one layer with the oracle's inputs rounded to BF16 agrees to FP32 rounding
 of K = 27 C_in products: 1e-5 of the layer's magnitude (sum of |terms|).  The
 network stores every activation and every layer gradient in BF16; the oracle
 rounds at the same points (rnd=bf16), so the two differ by FP32 accumulation
-and by the values whose rounding goes the other way after it: outputs 1e-2,
-gradients 5e-2 of each layer's norm.
+and by the values whose rounding (or ReLU mask) goes the other way after it:
+outputs 1e-2 of their norm; gradients 1e-1 of each layer's norm (a layer deep
+in the chain collects the most of those flips) and 3e-2 of the whole
+gradient's norm.
 """
 import numpy as np
 import pytest
@@ -133,8 +135,11 @@ def test_net_gradients(net_case):
     gref = U.backward(P, cache, dout, rnd=U.bf16)
     got = unflatten(N.get_grads(), P)
     for k, ((gw, gb), (rw, rb)) in enumerate(zip(got, gref)):
-        assert np.linalg.norm(gw - rw) < 5e-2 * np.linalg.norm(rw), k
-        assert np.linalg.norm(gb - rb) < 5e-2 * np.linalg.norm(rb) + 1e-7, k
+        assert np.linalg.norm(gw - rw) < 1e-1 * np.linalg.norm(rw), k
+        assert np.linalg.norm(gb - rb) < 1e-1 * np.linalg.norm(rb) + 1e-7, k
+    g_all = np.concatenate([np.concatenate([a.ravel(), b.ravel()]) for a, b in got])
+    r_all = np.concatenate([np.concatenate([a.ravel(), b.ravel()]) for a, b in gref])
+    assert np.linalg.norm(g_all - r_all) < 3e-2 * np.linalg.norm(r_all)
 
 
 def test_training_reduces_loss():

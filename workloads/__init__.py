@@ -85,6 +85,24 @@ def batch_problem(seed: int, sizes=(64, 96, 128, 160, 192)) -> Problem:
     return p
 
 
+def guess_problem(n: int, seed: int, bump_seed: int | None = None) -> Problem:
+    """One pair of the learned-guess workload: the three-ellipsoid geometry
+    drawn like ``ellipsoids_problem`` but with 2-4 ellipsoids (semi-axes
+    U[0.1,0.25], centres U[0.3,0.7]^3), Neumann on the ellipsoids, Dirichlet on
+    the box, and the manufactured right-hand side plus 20 Gaussian bumps (drawn
+    from ``bump_seed`` when given, so that one geometry can carry several)."""
+    rng = np.random.default_rng(30_000 + seed)
+    k = int(rng.integers(2, 5))
+    shapes = []
+    for _ in range(k):
+        c = rng.uniform(0.3, 0.7, 3)
+        a = rng.uniform(0.1, 0.25, 3)
+        shapes.append((c, a))
+    p = Problem(n, shapes, NEUMANN, (DIRICHLET,) * 6, f"guess_seed{seed}")
+    p.bumps = gaussian_bumps(shapes, seed=40_000 + (seed if bump_seed is None else 1_000_000 + bump_seed))
+    return p
+
+
 def inside_any(shapes, x, y, z):
     """True where the point lies inside (or on) any shape."""
     m = np.zeros(np.broadcast(x, y, z).shape, dtype=bool)

@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=1,
                     help="0 FP64 V-cycle; 1 FP32 grid work, FP64 LU-corrections; 2 FP32 grid work and "
                          "LU-correction factors (their PLG right-hand sides in double-float; FP64 bottom "
-                         "solve and outer residual)")
+                         "solve and outer residual); 3 as 1 with double-float LU-correction factors")
     ap.add_argument("--krylov", type=int, default=0, help="0 Alg. Multigrid, 1 GMRES right-preconditioned by the V-cycle")
     ap.add_argument("--min-n", type=int, default=16, help="coarsening stops before n < min-n")
     ap.add_argument("--restart", type=int, default=30)
@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape-bc", default="neumann", choices=["dirichlet", "neumann"],
                     help="boundary kind on the ellipsoids (the box is Dirichlet)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="single: the 256^3 solves; batch: --batch independent solves of mixed sizes")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "unet"],
+                    help="single: the 256^3 solves; batch: --batch independent solves of mixed sizes; "
+                         "unet: forward and training steps of the learned guess's network at --n")
     ap.add_argument("--batch", type=int, default=16, help="solves in the batch workload")
     ap.add_argument("--seed", type=int, default=0, help="first seed of the batch workload")
     return ap.parse_args()
@@ -449,7 +450,7 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic",
+            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic",
             "config": {"workload": workload(args, n), "n": n, "seeds": seeds, "unknowns_per_seed": Ns,
                        "unknowns": Ntot, "ms_per_solve": per_seed_ms,
                        "mean_ms_to_1e-10_per_solve": round(ms / len(seeds), 2),
@@ -462,7 +463,11 @@ def run_ours(args):
                                      "fp32 smoothing, residuals and transfers inside fp64 defect correction; fp64 "
                                      "LU-corrections, PLG rows, bottom solve and outer residual",
                                      "fp32 grid work and LU-correction factors (PLG right-hand sides in "
-                                     "double-float); fp64 bottom solve, outer residual"][args.precision],
+                                     "double-float); fp64 bottom solve, outer residual",
+                                     "fp32 smoothing, residuals and transfers inside fp64 defect correction; "
+                                     "LU-corrections with fp64 right-hand sides and double-float factors (fp32 "
+                                     "pairs, about 2^-44 of each row); fp64 PLG rows, bottom solve and outer "
+                                     "residual"][args.precision],
                        "outer": ["Alg. Multigrid (stationary)",
                                  f"flexible GMRES({args.restart}) preconditioned by the V-cycle, "
                                  f"{['modified', 'classical'][args.cgs]} Gram-Schmidt"][args.krylov],
@@ -554,6 +559,8 @@ def run_extras(args, ccmg, W, torch, stream, probs, inputs, phi_head, head_stats
     variants = {}
     mask0 = exact0 != 0.0
     for name, over, what in (
+            ("double_float_lu_factors", dict(precision=3, krylov=0),
+             "Alg. Multigrid, FP32 grid work, LU-correction factors as FP32 pairs in double-float (precision 3)"),
             ("fp32_lu_factors", dict(precision=2, krylov=0),
              "Alg. Multigrid, FP32 grid work and FP32 LU-correction factors (precision 2)"),
             ("fgmres_fp32_lu_factors", dict(precision=2, krylov=1),
@@ -676,7 +683,7 @@ def run_batch(args):
             "metric": "batched independent solves to 1e-10, total MDOF/s", "value": unknowns * world / ms_bat / 1e3,
             "unit": "MDOF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bat,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": ["f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic", "impl": "batch",
+            "dtype": ["f64", "f32+f64", "f32+f64", "f32+f64"][args.precision], "data": "synthetic", "impl": "batch",
             "config": {"workload": f"{args.batch} solves, sizes from {{64,96,128,160,192}}^3, 1-4 spheres or "
                                    f"ellipsoids, Gaussian-bump RHS, {args.shape_bc} on the shapes",
                        "sizes": [p.n for p in probs], "unknowns": unknowns, "setup_s": round(setup_s, 1),
@@ -688,12 +695,72 @@ def run_batch(args):
         S.close()
 
 
+UNET_LAYERS = [(16, 16), (16, 16), (32, 16), (32, 32), (64, 32), (64, 64), (128, 64), (128, 128),
+               (64, 192), (64, 64), (32, 96), (32, 32), (16, 48), (16, 16)]  # (C_out, C_in stored), level l = k // 2
+
+
+def unet_flops(n):
+    """Tensor-core flops of one forward pass: 2 x cells x 27 x C_in x C_out per 3x3x3 layer."""
+    levels = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    return sum(2.0 * (n >> l) ** 3 * 27 * ci * co for (co, ci), l in zip(UNET_LAYERS, levels))
+
+
+def run_unet(args):
+    """The learned guess's network alone: forward passes and training steps
+    (forward, input and weight gradients, Adam) at n^3, timed with CUDA events
+    on the network's calls; tensor-core flops counted from the layer shapes
+    (the weight gradient and the input gradient each cost one forward)."""
+    import torch
+
+    from paper_2410_05865_gb300 import ccnet
+    n = args.n
+    net = ccnet.Net(n, seed=0)
+    rng = np.random.default_rng(0)
+    inp = torch.from_numpy(rng.standard_normal((1, n ** 3 * 3)).astype(np.float32)).cuda()
+    tgt = torch.from_numpy(rng.standard_normal((1, n ** 3)).astype(np.float32)).cuda()
+    wts = torch.ones((1, n ** 3), dtype=torch.float32, device="cuda")
+    out = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(k):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3 / k
+
+    ms_f = timed(lambda: net.forward(n, inp[0], out), args.steps)
+    ms_t = timed(lambda: net.train_step(n, 1, inp, tgt, wts, 1e-4), args.steps)
+    fl = unet_flops(n)
+    peak = 1942.1
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    print(json.dumps({"metric": "U-Net (learned guess) forward / training step", "value": fl / (ms_f / 1e3) / 1e12,
+                      "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms_t, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "impl": "unet",
+                      "config": {"workload": f"3-D U-Net of include/ccnet.h at {n}^3, batch 1",
+                                 "params": net.num_params, "forward_ms": ms_f, "train_step_ms": ms_t,
+                                 "forward_gflop": fl / 1e9, "train_tflops": 3 * fl / (ms_t / 1e3) / 1e12,
+                                 "host_timer": "wall clock around synchronised calls"},
+                      "roofline": {"bound": "tensor", "achieved": fl / (ms_f / 1e3) / 1e12, "peak": peak,
+                                   "unit": "TFLOP/s", "frac": fl / (ms_f / 1e3) / 1e12 / peak}}))
+    net.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "unet":
+        run_unet(args)
     else:
         run_ours(args)
 

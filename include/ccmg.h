@@ -76,7 +76,7 @@ typedef struct {
   int min_coarse_n;  /* coarsening stops before n < min_coarse_n (16) */
   int max_levels;    /* (16) */
   int use_graph;     /* capture each V-cycle + outer update in a CUDA graph (1) */
-  int lu_leaf;       /* nested-dissection leaf size (64) */
+  int lu_leaf;       /* nested-dissection leaf size (128) */
   int host_threads;  /* OpenMP threads for the setup (0 = default) */
   int krylov;        /* 0: Alg. Multigrid (stationary, the paper); 1: restarted GMRES
                         right-preconditioned by the same V-cycle (0) */
@@ -88,7 +88,11 @@ typedef struct {
                         factors in FP32, their right-hand sides (from the PLG rows
                         and the FP32 grid values) summed in double-float FP32
                         arithmetic, about 2^-48 of the terms (the bottom solve and
-                        the outer residual stay FP64).  With 1 and 2, GMRES applies
+                        the outer residual stay FP64); 3: as 1, with the finer levels'
+                        LU-correction factors stored as FP32 pairs hi + lo and
+                        applied in double-float arithmetic on the FP32 pipe (about
+                        2^-44 of each row's terms; FP64 right-hand sides, work
+                        vectors and results).  With 1, 2 and 3, GMRES applies
                         the operator to the FP32 V-cycle output with exact
                         fixed-point interior rows (cc_residual_f32) (0) */
   int lu_schedule;   /* triangular sweeps of the LU-corrections and bottom solve:
@@ -222,10 +226,12 @@ cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_s
  * or device per `where`): f / s on the unknowns, the fluid volume fraction of
  * each cell, and the boundary data / s (a cell's patch average, else the mean
  * of the box-face averages of its faces on the box, else 0), with the data
- * scale s = RMS of f over the unknowns (1 if f vanishes) returned in *scale;
- * the solution of the data divided by s is the network's target.
- * cc_solve_learned runs the network on those inputs (its grid must hold the
- * solver's finest n), starts the solve from s times its output, and then
+ * scale s = RMS of f over the unknowns (1 if f vanishes).  *scale receives the
+ * output scale s / (3 pi^2): the network's target is the solution divided by
+ * it (3 pi^2, the lowest Dirichlet eigenvalue of the unit box, makes the
+ * targets O(1)).  cc_solve_learned runs the network on those inputs (its grid
+ * must hold the solver's finest n), starts the solve from *scale times its
+ * output, and then
  * iterates exactly as cc_solve (stats count the V-cycles after the guess;
  * ms_solve excludes the network). */
 typedef struct ccnet ccnet;
@@ -263,6 +269,7 @@ cc_status cc_lu_correction(cc_solver* s, int level, double* phi, const double* r
  *   phi, rhs   device grid arrays of `level` (FP64), as for cc_lu_correction;
  *              phi is updated in place on the solver's stream.
  * Limits and behaviour:
+ *   - precision 3 (double-float factors) is rejected with CC_ERR_INVALID_ARG;
  *   - the level's LU-correction may have at most 262144 phi2 rows; a larger one
  *     is rejected with CC_ERR_INVALID_ARG and a message (cc_last_error), and
  *     cc_lu_correction must be used instead; the bottom level is rejected too;

@@ -265,7 +265,7 @@ class Solver:
 
     def guess_inputs(self, f, g_box, g_patch, out):
         """The learned guess's input channels for the data (see cc_guess_inputs);
-        returns the data scale s."""
+        returns the output scale (the network's target is phi divided by it)."""
         where = CC_HOST if isinstance(out, np.ndarray) else CC_DEVICE
         sc = C.c_double()
         self._check(lib().cc_guess_inputs(self._h, _ptr(f), _ptr(g_box), _ptr(g_patch), _ptr(out), where,
@@ -397,9 +397,22 @@ def cell_averages(solver: Solver, fn, q=8):
     return out
 
 
-def cell_averages_terms(solver: Solver, terms, q=8):
+def cut_centroids(solver: Solver):
+    """(cut cells, their fluid centroids) from the library's cut-cell quadrature."""
+    cells, ptr, xyz, w = solver.cut_nodes()
+    if len(cells) == 0:
+        return cells, np.zeros((0, 3))
+    den = np.add.reduceat(w, ptr[:-1])
+    cen = np.stack([np.add.reduceat(xyz[:, d] * w, ptr[:-1]) / den for d in range(3)], 1)
+    return cells, cen
+
+
+def cell_averages_terms(solver: Solver, terms, q=8, cut_points=None):
     """cell_averages for f = sum_t coef_t fx_t(x) fy_t(y) fz_t(z): on full cells the
-    q^3 tensor Gauss-Legendre rule factorises into three 1-D rules."""
+    q^3 tensor Gauss-Legendre rule factorises into three 1-D rules.  With
+    cut_points = (cells, points) the cut cells take the value at those points
+    (e.g. their centroids: second-order, for quick data) instead of their
+    quadrature."""
     n = solver.n
     h = 1.0 / n
     kind, _, _, _ = solver.cell_map(0)
@@ -412,6 +425,14 @@ def cell_averages_terms(solver: Solver, terms, q=8):
         az = fz(pts) @ gw
         acc += coef * ax[:, None, None] * ay[None, :, None] * az[None, None, :]
     out = np.where(kind == 1, acc.reshape(-1), 0.0)
+    if cut_points is not None:
+        cells, pts = cut_points
+        if len(cells):
+            val = np.zeros(len(cells))
+            for coef, (fx, fy, fz) in terms:
+                val += coef * fx(pts[:, 0]) * fy(pts[:, 1]) * fz(pts[:, 2])
+            out[cells] = val
+        return out
     cells, ptr, xyz, w = solver.cut_nodes()
     if len(cells):
         val = np.zeros(len(w))

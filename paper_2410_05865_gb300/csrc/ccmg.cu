@@ -621,6 +621,73 @@ __global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
   for (int t = warp; t < ntasks; t += nwarps) run_tile<FWD, TV>(tasks[t], lane, vals, structs, b, x);
 }
 
+// The same tile with double-float factors: an FP64 entry stored as the FP32
+// pair hi + lo (|lo| <= 2^-24 |hi|), multiplied with the FP64 source split the
+// same way; each product's rounding error is recovered exactly by an FMA
+// (TwoProduct) and the running sum keeps its own by TwoSum (Knuth), so a row
+// is accurate to about 2^-44 of its terms while every operation runs on the
+// FP32 pipe (this GPU issues FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <bool FWD>
+__device__ __forceinline__ void run_tile_df(const Task& tk, int lane, const float2* __restrict__ vals,
+                                            const int* __restrict__ structs, double* b, double* x) {
+  const int nc = tk.ncols, ld = tk.ld;
+  const bool gather = !FWD && tk.src == 1;
+  const bool mine = lane < tk.nrows;
+  const float2* __restrict__ col = vals + tk.moff + (mine ? lane : 0);
+  float hi = 0.0f, lo = 0.0f;
+  for (int c0 = 0; c0 < nc; c0 += 32) {
+    const int c = c0 + lane;
+    double sv = 0.0;
+    if (c < nc) sv = gather ? __ldcg(x + structs[tk.soff + c]) : __ldcg(b + tk.soff + c);
+    const float sh = __double2float_rn(sv);
+    const float sl = __double2float_rn(sv - (double)sh);
+    const int cn = min(32, nc - c0);
+    constexpr int kBatch = 8;
+    for (int i = 0; i < cn; i += kBatch) {
+      float2 mv[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        mv[u] = i + u < cn ? __ldcs(col + (long long)(c0 + i + u) * ld) : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int srcl = (i + u) & 31;
+        const float xh = __shfl_sync(0xffffffffu, sh, srcl);
+        const float xl = __shfl_sync(0xffffffffu, sl, srcl);
+        const float p = mv[u].x * xh;
+        float e = __fmaf_rn(mv[u].x, xh, -p);
+        e = __fmaf_rn(mv[u].x, xl, __fmaf_rn(mv[u].y, xh, e));
+        float s2, t;
+        two_sum(hi, p, s2, t);
+        lo += t + e;
+        hi = s2;
+      }
+    }
+  }
+  if (mine) {
+    const double acc = (double)hi + (double)lo;
+    if (FWD)
+      atomicAdd(b + structs[tk.out + lane], -acc);
+    else
+      atomicAdd(x + tk.out + lane, tk.src == 1 ? -acc : acc);
+  }
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(256, 3)
+    k_tasks_df(const Task* __restrict__ tasks, int ntasks, const float2* __restrict__ vals,
+               const int* __restrict__ structs, double* b, double* x) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < ntasks; t += nwarps) run_tile_df<FWD>(tasks[t], lane, vals, structs, b, x);
+}
+
 // Grid-wide barrier of a cooperative launch (all blocks resident).  Arrivals
 // are counted in two levels (a block on its group's counter, the last block of
 // a group on the top counter) so no single address takes one atomic per
@@ -910,6 +977,8 @@ struct DevLU {
   bool f32 = false;          // factors and work vectors in FP32 (vals32, b32, x32)
   double* vals = nullptr;
   float* vals32 = nullptr;
+  float2* valsdf = nullptr;  // double-float factors (hi, lo) with FP64 work vectors (precision 3)
+  bool df = false;
   int* structs = nullptr;
   Task* tasks = nullptr;
   std::vector<long long> toff[2];  // per sweep (0 forward, 1 backward): task offsets by height (height+2)
@@ -1246,15 +1315,23 @@ void full_operator(const Level& L, const StencilP& P, std::vector<int>& uid, std
 
 cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<int>& pos_cell,
                     const std::vector<int>& rptr, const std::vector<int>& rcol, const std::vector<double>& rval,
-                    bool f32) {
+                    bool f32, bool df = false) {
   D.np = F.n;
   D.height = F.height;
   D.entries = F.nnz_factor;
   D.f32 = f32;
+  D.df = df && !f32;
   cc_status st;
   if (f32) {
     std::vector<float> v32(F.vals.begin(), F.vals.end());
     if ((st = dupload(S, &D.vals32, v32))) return st;
+  } else if (D.df) {
+    std::vector<float2> v2(F.vals.size());
+    for (size_t q = 0; q < F.vals.size(); ++q) {
+      const float hi = (float)F.vals[q];
+      v2[q] = make_float2(hi, (float)(F.vals[q] - (double)hi));
+    }
+    if ((st = dupload(S, &D.valsdf, v2))) return st;
   } else if ((st = dupload(S, &D.vals, F.vals))) {
     return st;
   }
@@ -1306,7 +1383,7 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
   if ((st = dalloc(S, &D.bar, 1 + kBarGroups))) return st;
   // one cooperative launch per solve when the device allows it: every block resident
   D.coop_grid = 0;
-  if (S->coop && S->prm.lu_schedule == 1) {
+  if (S->coop && S->prm.lu_schedule == 1 && !D.df) {
     int per_sm = 0;
     cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_sweeps<float>, 256, 0)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_sweeps<double>, 256, 0);
@@ -1413,9 +1490,40 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
   k_scatter<T, TV><<<grid_for(S, D.np, block), block, 0, S->stream>>>(x, D.np, D.cell, phi);
 }
 
+// The same solve with double-float factors (FP64 right-hand side, work vectors
+// and scatter; the sweeps' products on the FP32 pipe), per-height launches.
+template <class T>
+void lu_solve_df(cc_solver* S, const DevLU& D, const T* s, T* phi) {
+  if (D.np == 0) return;
+  const int block = 256;
+  {
+    ProfScope ps(S, P_LURHS, (8.0 + sizeof(T)) * D.np + (8.0 + 4.0 + sizeof(T)) * D.rnnz + 16.0 * D.np);
+    k_lu_rhs<T, double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.b, D.x, D.np, D.cell, D.rptr, D.rcol,
+                                                                          D.rval, s, phi, nullptr);
+  }
+  ProfScope sweep_scope(S, P_SWEEP, D.sweep_bytes, D.nsweep_launches);
+  for (int sw = 0; sw < 2; ++sw)
+    for (int k = 0; k <= D.height; ++k) {
+      const int h = sw == 0 ? k : D.height - k;
+      const long long a = D.toff[sw][h], e = D.toff[sw][h + 1];
+      const int nt = (int)(e - a);
+      if (nt <= 0) continue;
+      const int grid = grid_for(S, (long long)nt * 32, block);
+      if (sw == 0)
+        k_tasks_df<true><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, D.valsdf, D.structs, D.b, D.x);
+      else
+        k_tasks_df<false><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, D.valsdf, D.structs, D.b, D.x);
+    }
+  sweep_scope.close();
+  ProfScope ps(S, P_SCATTER, (8.0 + 4.0 + sizeof(T)) * D.np);
+  k_scatter<T, double><<<grid_for(S, D.np, block), block, 0, S->stream>>>(D.x, D.np, D.cell, phi);
+}
+
 template <class T>
 void lu_solve(cc_solver* S, DevLU& D, const T* s, T* phi) {
-  if (D.f32)
+  if (D.df)
+    lu_solve_df<T>(S, D, s, phi);
+  else if (D.f32)
     lu_solve_ws<T, float>(S, D, s, phi, D.b32, D.x32);
   else
     lu_solve_ws<T, double>(S, D, s, phi, D.b, D.x);
@@ -2030,7 +2138,7 @@ void cc_default_params(cc_params* p) {
   p->min_coarse_n = 16;
   p->max_levels = 16;
   p->use_graph = 1;
-  p->lu_leaf = 64;
+  p->lu_leaf = 128;
   p->host_threads = 0;
   p->krylov = 0;
   p->krylov_restart = 30;
@@ -2090,7 +2198,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   else
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
-      S->prm.precision < 0 || S->prm.precision > 2 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
+      S->prm.precision < 0 || S->prm.precision > 3 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
       S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1 ||
       S->prm.fmg < 0) {
     delete S;
@@ -2237,7 +2345,8 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
     TRY(dupload(S, &D.p2_col, L.p2_col));
     TRY(dupload(S, &D.p2_val, L.p2_val));
     // precision 2: the LU-corrections of the finer levels run in FP32; the bottom solve stays FP64
-    TRY(upload_lu(S, D.lu, lus[m], lu_cells[m], rptr[m], rcol[m], rval[m], S->prm.precision == 2 && m < M));
+    TRY(upload_lu(S, D.lu, lus[m], lu_cells[m], rptr[m], rcol[m], rval[m], S->prm.precision == 2 && m < M,
+                  S->prm.precision == 3 && m < M));
     TRY(dalloc(S, &D.s, D.N));
     TRY(dalloc(S, &D.e, D.N));
     TRY(dalloc(S, &D.tmp, D.N));
@@ -2484,7 +2593,8 @@ cc_status cc_solve(cc_solver* S, const double* f, const double* g_box, const dou
   return run_solve(S, phi, where, stats);
 }
 
-// data scale s = RMS of f over the unknowns (1 if f vanishes) and the learned-guess inputs in S->ginp
+// learned-guess inputs in S->ginp (data divided by s = RMS of f over the unknowns,
+// 1 if f vanishes) and the output scale s / (3 pi^2) in *scale
 static cc_status guess_inputs(cc_solver* S, const double* f, const double* g_box, const double* g_patch, int where,
                               double* scale) {
   cc_status st = build_rhs(S, f, g_box, g_patch, where);
@@ -2502,7 +2612,9 @@ static cc_status guess_inputs(cc_solver* S, const double* f, const double* g_box
   k_guess_inputs<<<grid_for(S, L.N, 256), 256, 0, S->stream>>>(S->f, S->gbox, S->gpatch, L.typ, S->vol0, S->cellpatch,
                                                                L.n, 1.0 / s, S->ginp);
   CK(cudaGetLastError());
-  *scale = s;
+  // output scale: the network predicts kappa phi / s, kappa = 3 pi^2 (the lowest
+  // Dirichlet eigenvalue of the unit box), which makes its targets O(1)
+  *scale = s / (3.0 * M_PI * M_PI);
   return CC_OK;
 }
 
@@ -2719,6 +2831,9 @@ cc_status cc_lu_correction_static(cc_solver* S, int level, double* phi, const do
   if (st) return st;
   if (level == (int)S->lev.size() - 1) return fail(S, CC_ERR_INVALID_ARG, "the bottom level has no LU-correction");
   const DevLU& D = S->lev[level].lu;
+  if (D.df)
+    return fail(S, CC_ERR_INVALID_ARG,
+                "cc_lu_correction_static: double-float factors (precision 3) are not supported; use cc_lu_correction");
   if (D.np > kStaticLuRows)
     return fail(S, CC_ERR_INVALID_ARG,
                 "cc_lu_correction_static: level " + std::to_string(level) + " has " + std::to_string(D.np) +

@@ -1,7 +1,7 @@
 """Training of the learned initial guess (include/ccnet.h) on pairs the solver
 generates: for random geometries and right-hand sides of the learned-guess
-workload, the multigrid solve gives phi, cc_guess_inputs the network's input,
-and the network is fitted to phi / s (s the data scale) on the unknowns by
+workload, the multigrid solve gives phi, cc_guess_inputs the network's input
+and the output scale c, and the network is fitted to phi / c on the unknowns by
 Adam steps of ccnet_train_step.  Every computation runs in libccmg.so; this
 module only sequences the calls.
 """
@@ -42,9 +42,12 @@ def make_pairs(n, seeds, device=0, solver_kw=None, rhs_per_geometry=1):
         gp = dev(ccmg.patch_averages(S, W.phi_exact, W.grad_phi_exact, prob.shape_bc))
         _, typ, _, _ = S.cell_map(0)
         live = dev((typ > 0).astype(np.float32))
+        # training data only need consistent (f, phi) pairs: cut cells take f at
+        # their centroid instead of the 20-bump sum over every quadrature node
+        cut = ccmg.cut_centroids(S)
         for k in range(rhs_per_geometry):
             pk = W.guess_problem(n, seed, bump_seed=seed * 100 + k)
-            f = dev(ccmg.cell_averages_terms(S, W.rhs_terms(pk)))
+            f = dev(ccmg.cell_averages_terms(S, W.rhs_terms(pk), cut_points=cut))
             phi = torch.zeros(V, dtype=torch.float64, device="cuda")
             st, rc = S.solve(f, gb, gp, phi)
             if rc != 0:

@@ -23,9 +23,9 @@ def trained():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2410_05865_gb300 import ccnet, train_guess
-    data = train_guess.make_pairs(N, list(range(4)), rhs_per_geometry=3)
+    data = train_guess.make_pairs(N, list(range(6)), rhs_per_geometry=4)
     net = ccnet.Net(N, seed=0)
-    hist = train_guess.train(net, N, data, steps=240, lr=1e-3, batch=2)
+    hist = train_guess.train(net, N, data, steps=400, lr=1e-3, batch=2)
     yield net, hist
     net.close()
 
@@ -48,8 +48,20 @@ def test_learned_start_saves_vcycles(trained):
     st0, rc0 = S.solve(f, gb, gp, phi0)
     phi1 = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
     st1, rc1 = S.solve_learned(net, f, gb, gp, phi1)
+    # the guess itself, against the converged solution
+    inp = torch.zeros(N ** 3 * 3, dtype=torch.float32, device="cuda")
+    scale = S.guess_inputs(f, gb, gp, inp)
+    out = torch.zeros(N ** 3, dtype=torch.float32, device="cuda")
+    net.forward(N, inp, out)
+    _, typ, _, _ = S.cell_map(0)
     S.close()
+    live = torch.from_numpy(typ > 0).cuda()
+    guess = out.double() * scale
+    err = float(torch.linalg.norm((guess - phi0)[live]) / torch.linalg.norm(phi0[live]))
+    print(f"guess rel error {err:.3e}; V-cycles zero start {st0.iters}, learned start {st1.iters}; "
+          f"first residuals {list(st0.resid_hist[:3])} vs {list(st1.resid_hist[:3])}")
     assert rc0 == 0 and rc1 == 0 and st1.rel_resid < 1e-10
+    assert err < 0.5
     assert st1.iters < st0.iters, (st0.iters, st1.iters)
     a, b = phi0.cpu().numpy(), phi1.cpu().numpy()
     assert np.abs(a - b).max() < 1e-7 * np.abs(a).max()

@@ -157,6 +157,25 @@ def test_lu_correction_parity(pair, level):
 
 
 @pytest.mark.parametrize("level", [0, 1])
+def test_df_lu_correction_parity(pair, level):
+    """SMO-2 with double-float factors (precision 3: FP64 entries stored as FP32
+    pairs, products and sums on the FP32 pipe with exact error terms) against
+    the oracle's FP64 LU-correction: 1e-9 relative (about 2^-44 per row,
+    times the growth of the triangular solves)."""
+    S, H, _, _, prob = pair
+    lv, ops = H.levels[level], H.ops[level]
+    K = solver(prob, precision=3)
+    phi = rand_unknowns(lv, 15)
+    s = rand_unknowns(lv, 16) * 1e3
+    g = dev(to_grid(lv, phi))
+    K.lu_correction(level, g, dev(to_grid(lv, s)))
+    K.sync()
+    K.close()
+    ref = MG.lu_correction(ops, phi, s)
+    assert rel(from_grid(lv, g.cpu()), ref, np.abs(ref).max()) < 1e-9
+
+
+@pytest.mark.parametrize("level", [0, 1])
 def test_restrict_parity(pair, level):
     S, H, _, _, _ = pair
     f, c = H.levels[level], H.levels[level + 1]
@@ -233,12 +252,13 @@ def test_trajectory_parity(pair):
         assert rel(from_grid(lv, phi.cpu()), ref, np.abs(ref).max()) < 1e-10, k
 
 
-def test_fp32_vcycle_parity(pair):
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_fp32_vcycle_parity(pair, precision):
     """The FP32 V-cycle (precision 2: FP32 Jacobi, residual, restriction and
     trilinear prolongation, FP32 LU-correction factors with double-float
     right-hand sides, FP64 bottom solve) against the oracle's FP64 V-cycle."""
     S, H, _, r_or, prob = pair
-    K = solver(prob, precision=2)
+    K = solver(prob, precision=precision)
     lv = H.levels[0]
     e = torch.zeros(lv.n ** 3, dtype=torch.float64, device="cuda")
     K.vcycle(dev(to_grid(lv, r_or)), e)

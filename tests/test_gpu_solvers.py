@@ -69,7 +69,7 @@ def test_gmres_acceleration(case, flexible, cgs):
     assert err < 1e-7
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 @pytest.mark.parametrize("krylov", [0, 1])
 def test_mixed_precision_solve(case, krylov, precision):
     """FP32 grid work (precision 1), and also FP32 LU-correction factors

@@ -47,7 +47,7 @@ typedef enum {
   CC_ERR_PLG = 4,          /* no poised lattice on the finest level */
   CC_ERR_SINGULAR = 5,     /* zero or tiny pivot in an LU factorisation */
   CC_ERR_NOT_CONVERGED = 6,
-  CC_ERR_DIVERGED = 7,     /* non-finite residual */
+  CC_ERR_DIVERGED = 7,     /* residual not finite, or grown 1e4-fold above its start and ||r|| */
   CC_ERR_MERGE = 8,        /* cell merging could not make every cell theta-proper */
   CC_ERR_TIMEOUT = 9       /* a bounded wait in the one-launch LU sweeps ran out */
 } cc_status;
@@ -123,6 +123,9 @@ typedef struct {
                         level below prolongated into all unknowns and improved by k
                         V-cycles; the finest level starts from the prolongated solution
                         and the solve's V-cycles follow (stats count those only) (0) */
+  int lu_barrier_spins; /* bound on the polls of one grid-barrier wait of the one-launch
+                        LU sweeps (lu_schedule = 1); past it the sweep stops and the
+                        call returns CC_ERR_TIMEOUT.  0: 2^24 polls, about a second (0) */
 } cc_params;
 
 typedef struct {

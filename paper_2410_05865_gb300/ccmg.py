@@ -46,7 +46,8 @@ class cc_params(C.Structure):
                 ("use_graph", C.c_int), ("lu_leaf", C.c_int), ("host_threads", C.c_int),
                 ("krylov", C.c_int), ("krylov_restart", C.c_int), ("precision", C.c_int),
                 ("lu_schedule", C.c_int), ("krylov_cgs", C.c_int), ("prolong", C.c_int),
-                ("restriction", C.c_int), ("krylov_flexible", C.c_int), ("fmg", C.c_int)]
+                ("restriction", C.c_int), ("krylov_flexible", C.c_int), ("fmg", C.c_int),
+                ("lu_barrier_spins", C.c_int)]
 
 
 class cc_stats(C.Structure):

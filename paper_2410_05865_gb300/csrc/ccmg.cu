@@ -696,7 +696,8 @@ __global__ void __launch_bounds__(256, 3)
 // next barrier, so the kernel always ends.
 constexpr long long kBarrierSpins = 1ll << 24;  // about a second of polling
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int phase, unsigned int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int phase, unsigned int* err,
+                                             long long spin_limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -707,7 +708,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int pha
     const unsigned int target = phase * ngroups;
     long long spins = 0;
     while (*(volatile unsigned int*)bar < target && *(volatile unsigned int*)err == 0u) {
-      if (++spins > kBarrierSpins) {
+      if (++spins > spin_limit) {
         atomicExch(err, 1u);
         break;
       }
@@ -726,7 +727,8 @@ template <class TV>
 __global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
     k_lu_sweeps(const Task* __restrict__ tasks, const long long* __restrict__ toff_f,
                 const long long* __restrict__ toff_b, int height, const TV* __restrict__ vals,
-                const int* __restrict__ structs, TV* b, TV* x, unsigned int* bar, unsigned int* err) {
+                const int* __restrict__ structs, TV* b, TV* x, unsigned int* bar, unsigned int* err,
+                long long spin_limit) {
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -734,12 +736,12 @@ __global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
   for (int h = 0; h <= height; ++h) {
     const long long e = toff_f[h + 1];
     for (long long t = toff_f[h] + warp; t < e; t += nwarps) run_tile<true, TV>(tasks[t], lane, vals, structs, b, x);
-    if (!grid_barrier(bar, ++phase, err)) return;
+    if (!grid_barrier(bar, ++phase, err, spin_limit)) return;
   }
   for (int h = height; h >= 0; --h) {
     const long long e = toff_b[h + 1];
     for (long long t = toff_b[h] + warp; t < e; t += nwarps) run_tile<false, TV>(tasks[t], lane, vals, structs, b, x);
-    if (h > 0 && !grid_barrier(bar, ++phase, err)) return;
+    if (h > 0 && !grid_barrier(bar, ++phase, err, spin_limit)) return;
   }
 }
 
@@ -1474,7 +1476,8 @@ void lu_solve_ws(cc_solver* S, const DevLU& D, const T* s, T* phi, TV* b, TV* x)
     const cudaError_t le =
         cudaLaunchKernelEx(&cfg, k_lu_sweeps<TV>, (const Task*)D.tasks, (const long long*)D.dtoff[0],
                            (const long long*)D.dtoff[1], D.height, vals, (const int*)D.structs, b, x, D.bar,
-                           S->err_flag);
+                           S->err_flag,
+                           S->prm.lu_barrier_spins > 0 ? (long long)S->prm.lu_barrier_spins : kBarrierSpins);
     if (le != cudaSuccess) {  // refused (e.g. not resident): report it and leave the solve to the caller's check
       S->err = std::string("cooperative LU sweep launch: ") + cudaGetErrorString(le);
       cudaGetLastError();
@@ -1832,11 +1835,14 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
   int it = 0;
   double rel = 0;
   const bool use_graph = S->prm.use_graph != 0;
+  double rel0 = 0.0;
   for (;; ++it) {
     if (S->prof) prof_flush(S);
     rel = rn > 0 ? std::sqrt(*S->hnorm) / rn : 0.0;
     if (stats && it < 256) stats->resid_hist[it] = rel;
-    if (!std::isfinite(rel)) {
+    if (it == 0) rel0 = rel;
+    // a non-finite residual, or one grown 1e4-fold above its start (and above ||r||)
+    if (!std::isfinite(rel) || (it > 0 && rel > 1e4 * std::max(1.0, rel0))) {
       result = CC_ERR_DIVERGED;
       break;
     }
@@ -1886,7 +1892,7 @@ cc_status solve_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     stats->ms_solve = ms;
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter";
-  if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (result == CC_ERR_DIVERGED) S->err = "the residual is not finite or grew 1e4-fold above its start";
   if (take_timeout(S)) {
     S->err = "a grid barrier of the LU sweeps waited too long";
     return CC_ERR_TIMEOUT;
@@ -2081,7 +2087,7 @@ cc_status gmres_loop(cc_solver* S, double* phi_out, int where, cc_stats* stats) 
     stats->ms_solve = ms;
   }
   if (result == CC_ERR_NOT_CONVERGED) S->err = "not converged within max_iter V-cycles";
-  if (result == CC_ERR_DIVERGED) S->err = "non-finite residual";
+  if (result == CC_ERR_DIVERGED) S->err = "the residual is not finite or grew 1e4-fold above its start";
   if (take_timeout(S)) {
     S->err = "a grid barrier of the LU sweeps waited too long";
     return CC_ERR_TIMEOUT;
@@ -2149,6 +2155,7 @@ void cc_default_params(cc_params* p) {
   p->restriction = 0;
   p->krylov_flexible = 1;
   p->fmg = 0;
+  p->lu_barrier_spins = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -2200,7 +2207,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
       S->prm.precision < 0 || S->prm.precision > 3 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
       S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1 ||
-      S->prm.fmg < 0) {
+      S->prm.fmg < 0 || S->prm.lu_barrier_spins < 0) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }

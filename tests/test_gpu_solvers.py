@@ -111,3 +111,46 @@ def test_smo1_tiles_tuned(case):
     for m in range(K.info.n_levels - 1):
         assert tuple(K.info.jacobi_block[m]) in cands
     K.close()
+
+
+def test_lu_barrier_timeout(case):
+    """A grid barrier of the one-launch LU sweeps that gives up after one poll
+    ends the sweep early and the call reports CC_ERR_TIMEOUT; the GPU context
+    stays usable (a default solver solves afterwards).  No wait is left open:
+    every block returns at its next barrier once the flag is raised."""
+    from paper_2410_05865_gb300 import ccmg
+    prob, (f, gb, gp), lv, ref, it = case
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N, lu_schedule=1,
+                    lu_barrier_spins=1)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    s = torch.ones(N ** 3, dtype=torch.float64, device="cuda")
+    codes = []
+    for _ in range(3):
+        try:
+            K.lu_correction(0, phi, s)
+            K.sync()
+            codes.append(0)
+        except ccmg.CCError as e:
+            codes.append(e.status)
+    K.close()
+    assert 9 in codes, codes  # CC_ERR_TIMEOUT
+    st, rc, err = run(case)
+    assert rc == 0 and err < 1e-7
+
+
+def test_diverging_iteration_reported(case):
+    """omega = 3 makes Jacobi amplify the high frequencies: the stationary
+    iteration's residual grows and the solve returns CC_ERR_DIVERGED instead of
+    running to max_iter."""
+    from paper_2410_05865_gb300 import ccmg
+    prob, (f, gb, gp), lv, ref, it = case
+    K = ccmg.Solver(N, prob.shapes, prob.shape_bc, prob.box_bc, device=0, min_coarse_n=MIN_N, omega=3.0,
+                    max_iter=400)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    st, rc = None, None
+    try:
+        st, rc = K.solve(dev(f), dev(gb), dev(gp), phi)
+    except ccmg.CCError as e:
+        rc = e.status
+    K.close()
+    assert rc == 7, rc

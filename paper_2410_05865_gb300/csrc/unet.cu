@@ -4,7 +4,8 @@
 // Tensor-core path (sm_103a): one CTA of 128 threads computes a tile of 128
 // output cells x C_out channels.  Per tap (27 of them) the threads gather their
 // cell's C_in input channels (zero outside the grid) and the tap's weights into
-// shared memory in the canonical K-major layout without swizzle (8-row x
+// shared memory (several taps side by side along K when C_in is small, up to
+// K = 256 per stage) in the canonical K-major layout without swizzle (8-row x
 // 16-byte core matrices, core matrix (row/8, k/8) at ((row/8) * K/8 + k/8) * 128
 // bytes), one elected thread issues C_in/16 tcgen05.mma (kind::f16, BF16
 // operands, FP32 accumulator of 128 lanes x C_out columns in tensor memory)
@@ -135,6 +136,7 @@ struct ConvFwd {
   int cin, cout;                 // channels, multiples of 16
   int xstride, ystride, ycol;    // row strides (elements) of x and y, y's first column
   int taps;                      // 27 (3x3x3) or 1 (1x1x1 at the centre)
+  int tps;                       // taps per shared-memory stage (divides taps; tps * cin <= 256)
   const __nv_bfloat16* x;        // [n^3][xstride], channels 0..cin-1 read
   const __nv_bfloat16* w;        // [cout][taps][cin]
   const float* bias;             // [cout] or null
@@ -148,8 +150,8 @@ struct ConvFwd {
 // Shared memory of the forward kernel: A tile 128 x cin, B tile cout x cin (BF16),
 // the B region sized for 256 rows so that no decoding of the MMA shape reads
 // past the allocation.
-__host__ __device__ inline size_t fwd_smem_bytes(int cin) {
-  return (size_t)kTileM * cin * 2 + (size_t)256 * cin * 2 + 64;
+__host__ __device__ inline size_t fwd_smem_bytes(int kst) {
+  return (size_t)kTileM * kst * 2 + (size_t)256 * kst * 2 + 64;
 }
 
 __global__ void __launch_bounds__(128) k_conv_fwd(ConvFwd p) {
@@ -157,8 +159,9 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvFwd p) {
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int kst = p.tps * p.cin;  // K of one stage
   unsigned char* As = smem;
-  unsigned char* Bs = smem + (size_t)kTileM * p.cin * 2;
+  unsigned char* Bs = smem + (size_t)kTileM * kst * 2;
   const int n = p.n;
   const long long V = (long long)n * n * n;
   const long long v = (long long)blockIdx.x * kTileM + tid;
@@ -178,42 +181,49 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvFwd p) {
   tc_fence_after();
   const uint32_t taddr = tslot;
   const uint32_t idesc = idesc_bf16(kTileM, p.cout);
-  const int kchunks = p.cin >> 3;  // 16-byte chunks per row
+  const int kchunks = p.cin >> 3;   // 16-byte chunks per tap and row
+  const int schunks = kst >> 3;     // 16-byte chunks per stage and row
+  const int nstages = p.taps / p.tps;
   bool ok = true;
   int issued = 0;
-  for (int t = 0; t < p.taps && ok; ++t) {
-    if (t > 0) {
-      const bool got = mbar_wait(&bar, (uint32_t)((t - 1) & 1));
+  for (int st = 0; st < nstages && ok; ++st) {
+    if (st > 0) {
+      const bool got = mbar_wait(&bar, (uint32_t)((st - 1) & 1));
       ok = !__syncthreads_or(!got);
       if (!ok) break;
     }
-    // A: this thread's cell, tap t
-    const int a = p.taps == 27 ? t / 9 - 1 : 0, b = p.taps == 27 ? (t / 3) % 3 - 1 : 0, c = p.taps == 27 ? t % 3 - 1 : 0;
-    const int ni = ci + a, nj = cj + b, nk = ck + c;
-    const bool in = v < V && ni >= 0 && ni < n && nj >= 0 && nj < n && nk >= 0 && nk < n;
-    const uint4* src = in ? reinterpret_cast<const uint4*>(p.x + (((long long)ni * n + nj) * n + nk) * p.xstride)
-                          : nullptr;
-    for (int q = 0; q < kchunks; ++q) {
-      const uint4 val = in ? src[q] : make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(As + kmajor_off(tid, q * 8, p.cin)) = val;
+    // A: this thread's cell, the stage's taps side by side along K
+    for (int j = 0; j < p.tps; ++j) {
+      const int t = st * p.tps + j;
+      const int a = p.taps == 27 ? t / 9 - 1 : 0, b = p.taps == 27 ? (t / 3) % 3 - 1 : 0,
+                c = p.taps == 27 ? t % 3 - 1 : 0;
+      const int ni = ci + a, nj = cj + b, nk = ck + c;
+      const bool in = v < V && ni >= 0 && ni < n && nj >= 0 && nj < n && nk >= 0 && nk < n;
+      const uint4* src = in ? reinterpret_cast<const uint4*>(p.x + (((long long)ni * n + nj) * n + nk) * p.xstride)
+                            : nullptr;
+      for (int q = 0; q < kchunks; ++q) {
+        const uint4 val = in ? src[q] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(As + kmajor_off(tid, j * p.cin + q * 8, kst)) = val;
+      }
     }
-    // B: weights of tap t, cout x cin
-    const int bchunks = p.cout * kchunks;
+    // B: the stage's weights, cout x (tps * cin), contiguous per output channel
+    const int bchunks = p.cout * schunks;
     for (int e = tid; e < bchunks; e += kTileM) {
-      const int co = e / kchunks, q = e % kchunks;
-      const uint4 val = *reinterpret_cast<const uint4*>(p.w + ((long long)co * p.taps + t) * p.cin + q * 8);
-      *reinterpret_cast<uint4*>(Bs + kmajor_off(co, q * 8, p.cin)) = val;
+      const int co = e / schunks, q = e % schunks;
+      const uint4 val =
+          *reinterpret_cast<const uint4*>(p.w + ((long long)co * p.taps + st * p.tps) * p.cin + q * 8);
+      *reinterpret_cast<uint4*>(Bs + kmajor_off(co, q * 8, kst)) = val;
     }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-      const uint32_t sbo = (uint32_t)kchunks << 7, lbo = 128u;
-      for (int s = 0; s < (p.cin >> 4); ++s) {
+      const uint32_t sbo = (uint32_t)schunks << 7, lbo = 128u;
+      for (int s = 0; s < (kst >> 4); ++s) {
         const uint64_t ad = sdesc(a0 + (uint32_t)(s * 256), lbo, sbo);
         const uint64_t bd = sdesc(b0 + (uint32_t)(s * 256), lbo, sbo);
-        mma_bf16(taddr, ad, bd, idesc, (t > 0 || s > 0) ? 1u : 0u);
+        mma_bf16(taddr, ad, bd, idesc, (st > 0 || s > 0) ? 1u : 0u);
       }
       mma_commit(&bar);
     }
@@ -410,8 +420,15 @@ int sm_count(int device) {
   return g_sm_count > 0 ? g_sm_count : 152;
 }
 
-cudaError_t launch_fwd(const ConvFwd& p, cudaStream_t st) {
-  const size_t sm = fwd_smem_bytes(p.cin);
+cudaError_t launch_fwd(ConvFwd p, cudaStream_t st) {
+  // the most taps per stage (of 27, 9, 3, 1 that divide the tap count) with K <= 256
+  p.tps = 1;
+  for (int t : {27, 9, 3})
+    if (p.taps % t == 0 && t * p.cin <= 256) {
+      p.tps = t;
+      break;
+    }
+  const size_t sm = fwd_smem_bytes(p.tps * p.cin);
   cudaError_t e = cudaFuncSetAttribute(k_conv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long long V = (long long)p.n * p.n * p.n;

@@ -147,11 +147,10 @@ struct ConvFwd {
   uint32_t tcols;                // tensor-memory columns to allocate
 };
 
-// Shared memory of the forward kernel: A tile 128 x cin, B tile cout x cin (BF16),
-// the B region sized for 256 rows so that no decoding of the MMA shape reads
-// past the allocation.
-__host__ __device__ inline size_t fwd_smem_bytes(int kst) {
-  return (size_t)kTileM * kst * 2 + (size_t)256 * kst * 2 + 64;
+// Shared memory of the forward kernel: A tile 128 x K, B tile cout x K (BF16),
+// K the stage's taps x cin.
+__host__ __device__ inline size_t fwd_smem_bytes(int kst, int cout) {
+  return (size_t)kTileM * kst * 2 + (size_t)cout * kst * 2 + 64;
 }
 
 __global__ void __launch_bounds__(128) k_conv_fwd(ConvFwd p) {
@@ -428,7 +427,7 @@ cudaError_t launch_fwd(ConvFwd p, cudaStream_t st) {
       p.tps = t;
       break;
     }
-  const size_t sm = fwd_smem_bytes(p.tps * p.cin);
+  const size_t sm = fwd_smem_bytes(p.tps * p.cin, p.cout);
   cudaError_t e = cudaFuncSetAttribute(k_conv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long long V = (long long)p.n * p.n * p.n;

@@ -96,9 +96,13 @@ typedef struct {
                         the operator to the FP32 V-cycle output with exact
                         fixed-point interior rows (cc_residual_f32) (0) */
   int lu_schedule;   /* triangular sweeps of the LU-corrections and bottom solve:
-                        0 one launch per tree height and sweep; 1 one cooperative
+                        0 one launch per tree height and sweep, each launched as a
+                        programmatic dependent of the one before (its blocks are
+                        scheduled and prefetch their first factor tile while the
+                        previous height drains, then wait for it); 1 one cooperative
                         launch per solve with bounded grid barriers between heights
-                        (falls back to 0 where cooperative launch is unavailable) (0) */
+                        (falls back to 2 where cooperative launch is unavailable);
+                        2 as 0 with plain stream-ordered launches (0) */
   int krylov_cgs;    /* GMRES orthogonalisation: 0 modified Gram-Schmidt (a dot and an
                         update per basis vector); 1 classical Gram-Schmidt in two
                         fused passes over the basis (0) */

@@ -489,6 +489,17 @@ __global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi,
 
 constexpr int kBarGroups = 16;  // group counters of the one-launch sweeps' grid barrier (after one top counter)
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation may be scheduled while its predecessor is
+// still running; it touches nothing that the predecessor writes before
+// pdl_wait(), which returns once the predecessor grid has completed and its
+// memory operations are visible (at once for a kernel launched without the
+// attribute).  pdl_trigger() lets such a successor's blocks be scheduled as
+// this grid's blocks retire, hiding its launch and first loads behind the
+// tail of this grid.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // b[p] = s[cell[p]] - sum_q val_q phi[col_q]   (rows in nested-dissection order)
 // The PLG rows are applied in FP64 (k_lu_rhs_df below serves the FP32 grids
 // whose factors are FP32 too); b is stored in the LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
@@ -496,6 +507,7 @@ template <class T, class TW>
 __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                          const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
                          const T* __restrict__ s, const T* __restrict__ phi, unsigned int* __restrict__ bar) {
+  pdl_trigger();  // the first sweep launch may be scheduled; it waits for this grid
   if (bar && blockIdx.x == 0 && threadIdx.x <= kBarGroups) bar[threadIdx.x] = 0u;  // one-launch sweep counters
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     double v = (double)s[cell[p]];
@@ -516,6 +528,7 @@ template <class TW>
 __global__ void k_lu_rhs_df(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                             const int* __restrict__ ptr, const int* __restrict__ col, const float2* __restrict__ val,
                             const float* __restrict__ s, const float* __restrict__ phi, unsigned int* __restrict__ bar) {
+  pdl_trigger();
   if (bar && blockIdx.x == 0 && threadIdx.x <= kBarGroups) bar[threadIdx.x] = 0u;  // one-launch sweep counters
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     float hi = s[cell[p]], lo = 0.0f;
@@ -610,14 +623,33 @@ __device__ __forceinline__ void run_tile(const Task& tk, int lane, const TV* __r
   }
 }
 
-// One tree height of one sweep (the launch-per-height schedule).
+// Before the wait of a programmatic launch: pull the warp's first tile (factor
+// entries only, which no earlier launch writes) towards L2, so that its first
+// loads after the wait do not pay the full DRAM latency.
+template <class TE>
+__device__ __forceinline__ void prefetch_tile(const Task& tk, int lane, const TE* __restrict__ vals) {
+  if (lane < tk.nrows) {
+    const TE* col = vals + tk.moff + lane;
+    for (int c = 0; c < tk.ncols; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(col + (long long)c * tk.ld));
+  }
+}
+
+// Blocks resident per SM of the sweep kernels (their launch bounds).
+template <class TV>
+constexpr int sweep_blocks_per_sm() { return sizeof(TV) == 4 ? 4 : 3; }
+
+// One tree height of one sweep (the launch-per-height schedule); the grid is
+// at most the resident blocks, each warp striding over the tiles.
 template <bool FWD, class TV>
-__global__ void __launch_bounds__(256, sizeof(TV) == 4 ? 4 : 3)
+__global__ void __launch_bounds__(256, sweep_blocks_per_sm<TV>())
     k_tasks(const Task* __restrict__ tasks, int ntasks, const TV* __restrict__ vals, const int* __restrict__ structs,
             TV* b, TV* x) {
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (warp < ntasks) prefetch_tile(tasks[warp], lane, vals);
+  pdl_wait();
   for (int t = warp; t < ntasks; t += nwarps) run_tile<FWD, TV>(tasks[t], lane, vals, structs, b, x);
 }
 
@@ -682,9 +714,12 @@ template <bool FWD>
 __global__ void __launch_bounds__(256, 3)
     k_tasks_df(const Task* __restrict__ tasks, int ntasks, const float2* __restrict__ vals,
                const int* __restrict__ structs, double* b, double* x) {
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (warp < ntasks) prefetch_tile(tasks[warp], lane, vals);
+  pdl_wait();
   for (int t = warp; t < ntasks; t += nwarps) run_tile_df<FWD>(tasks[t], lane, vals, structs, b, x);
 }
 
@@ -1427,17 +1462,44 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
 }
 
 // --------------------------------------------------------------- launches
+// A launch on the solver's stream, with programmatic stream serialisation when
+// pdl is set (the kernel must call pdl_wait() before reading what earlier
+// launches write).
+template <class... KArgs, class... Args>
+void launch_k(cc_solver* S, void (*kern)(KArgs...), int grid, int block, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = S->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Grid of one sweep launch over nt warp tiles: one warp per tile, at most the
+// blocks that are resident at once (the warps then stride over the tiles).
+int sweep_grid(const cc_solver* S, int nt, int per_sm) {
+  const long long want = ((long long)nt + 7) / 8;
+  const long long cap = (long long)per_sm * S->nsm;
+  return (int)std::max(1ll, std::min(want, cap));
+}
+
 template <class TV>
 void launch_sweep(cc_solver* S, const DevLU& D, const TV* vals, int sweep, int h, TV* b, TV* x) {
   const long long a = D.toff[sweep][h], e = D.toff[sweep][h + 1];
   const int nt = (int)(e - a);
   if (nt <= 0) return;
-  const int block = 256;
-  const int grid = grid_for(S, (long long)nt * 32, block);
+  const int grid = sweep_grid(S, nt, sweep_blocks_per_sm<TV>());
+  const bool pdl = S->prm.lu_schedule == 0;
   if (sweep == 0)
-    k_tasks<true, TV><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, vals, D.structs, b, x);
+    launch_k(S, k_tasks<true, TV>, grid, 256, pdl, (const Task*)(D.tasks + a), nt, vals, (const int*)D.structs, b, x);
   else
-    k_tasks<false, TV><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, vals, D.structs, b, x);
+    launch_k(S, k_tasks<false, TV>, grid, 256, pdl, (const Task*)(D.tasks + a), nt, vals, (const int*)D.structs, b,
+             x);
 }
 
 // phi[cells] = A^{-1} (s[cells] - R phi) with the stored factors, on work vectors b and x
@@ -1511,11 +1573,14 @@ void lu_solve_df(cc_solver* S, const DevLU& D, const T* s, T* phi) {
       const long long a = D.toff[sw][h], e = D.toff[sw][h + 1];
       const int nt = (int)(e - a);
       if (nt <= 0) continue;
-      const int grid = grid_for(S, (long long)nt * 32, block);
+      const int grid = sweep_grid(S, nt, 3);
+      const bool pdl = S->prm.lu_schedule == 0;
       if (sw == 0)
-        k_tasks_df<true><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, D.valsdf, D.structs, D.b, D.x);
+        launch_k(S, k_tasks_df<true>, grid, block, pdl, (const Task*)(D.tasks + a), nt, (const float2*)D.valsdf,
+                 (const int*)D.structs, D.b, D.x);
       else
-        k_tasks_df<false><<<grid, block, 0, S->stream>>>(D.tasks + a, nt, D.valsdf, D.structs, D.b, D.x);
+        launch_k(S, k_tasks_df<false>, grid, block, pdl, (const Task*)(D.tasks + a), nt, (const float2*)D.valsdf,
+                 (const int*)D.structs, D.b, D.x);
     }
   sweep_scope.close();
   ProfScope ps(S, P_SCATTER, (8.0 + 4.0 + sizeof(T)) * D.np);
@@ -2232,7 +2297,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   else
     cc_default_params(&S->prm);
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
-      S->prm.precision < 0 || S->prm.precision > 3 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 1 ||
+      S->prm.precision < 0 || S->prm.precision > 3 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 2 ||
       S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1 ||
       S->prm.fmg < 0 || S->prm.lu_barrier_spins < 0) {
     delete S;

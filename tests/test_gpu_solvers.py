@@ -93,12 +93,19 @@ def test_transfer_options_solve(case, prolong, restriction):
         assert abs(st.iters - case[4]) <= 1  # the oracle runs this V-cycle
 
 
-def test_lu_schedules_agree(case):
-    """The one-launch cooperative sweep schedule gives the same solve as one
-    launch per tree height."""
-    st, rc, err = run(case, lu_schedule=1)
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_lu_schedules_agree(case, schedule):
+    """The one-launch cooperative sweep schedule (1) and plain stream-ordered
+    per-height launches (2) give the same solve as the default per-height
+    launches with programmatic dependencies, V-cycle for V-cycle."""
+    st0, rc0, err0 = run(case)
+    st, rc, err = run(case, lu_schedule=schedule)
     assert rc == 0 and st.rel_resid < 1e-10
     assert err < 1e-7
+    assert st.iters == st0.iters
+    h0 = np.array(st0.resid_hist[:st0.iters])
+    h = np.array(st.resid_hist[:st.iters])
+    assert np.allclose(h, h0, rtol=1e-6, atol=0)
 
 
 def test_smo1_tiles_tuned(case):

@@ -49,7 +49,7 @@ typedef enum {
   CC_ERR_NOT_CONVERGED = 6,
   CC_ERR_DIVERGED = 7,     /* residual not finite, or grown 1e4-fold above its start and ||r|| */
   CC_ERR_MERGE = 8,        /* cell merging could not make every cell theta-proper */
-  CC_ERR_TIMEOUT = 9       /* a bounded wait in the one-launch LU sweeps ran out */
+  CC_ERR_TIMEOUT = 9       /* a bounded wait (one-launch LU sweeps, persistent batch) ran out */
 } cc_status;
 
 enum { CC_DIRICHLET = 0, CC_NEUMANN = 1 };
@@ -128,8 +128,10 @@ typedef struct {
                         V-cycles; the finest level starts from the prolongated solution
                         and the solve's V-cycles follow (stats count those only) (0) */
   int lu_barrier_spins; /* bound on the polls of one grid-barrier wait of the one-launch
-                        LU sweeps (lu_schedule = 1); past it the sweep stops and the
-                        call returns CC_ERR_TIMEOUT.  0: 2^24 polls, about a second (0) */
+                        LU sweeps (lu_schedule = 1) and of one segment wait of the
+                        persistent batch (cc_solve_batch_persistent, first solver's
+                        value); past it the launch stops and the call returns
+                        CC_ERR_TIMEOUT.  0: 2^24 polls, about a second (0) */
 } cc_params;
 
 typedef struct {
@@ -195,7 +197,10 @@ cc_status cc_patch_nodes(const cc_solver* s, int32_t* owners, int64_t* ptr, doub
  * cols[nnz] (grid indices), vals[nnz] (entries of L); boundary terms bptr,
  * bpatch (patch number, finest level only; a box-face term of a row next to the
  * box is coded -(1 + face id), face ids as for g_box), bcoef (coefficient of
- * <<g>>, or of the box face's <g>). */
+ * <<g>>, or of the box face's <g>).  Any pointer may be NULL (not written).
+ * bptr[n_phi2] boundary terms are written to bpatch and bcoef; a lattice cell
+ * can add a patch term and up to three box-face terms, so on coarse levels
+ * near the box that count can exceed nnz: query bptr alone first. */
 cc_status cc_phi2_rows(const cc_solver* s, int level, int32_t* cells, int32_t* ptr, int32_t* cols, double* vals,
                        int32_t* bptr, int32_t* bpatch, double* bcoef);
 
@@ -224,6 +229,28 @@ cc_status cc_solve(cc_solver* s, const double* f, const double* g_box, const dou
 cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, const double* const* g_box,
                          const double* const* g_patch, double* const* phi, int where, cc_stats* stats,
                          cc_status* status);
+/* The same batch with every V-cycle of all solves in one persistent launch
+ * (no paper counterpart).  One iteration of Alg. Multigrid of each solve (the
+ * precision-1 V-cycle of cc_solve: SMO-1, LU-corrections by tree height,
+ * restriction, bottom solve, prolongation; then phi += e and the recursive
+ * residual s -= L e with its norm) is listed as a chain of segments, each a
+ * set of tiles (a block of cells, rows or eight LU warp tiles); the segments
+ * of all solves are interleaved step by step and numbered by a running ticket.
+ * Each block of the launch takes the next ticket, waits (at most the first
+ * solver's params.lu_barrier_spins polls, by default about a second) until the
+ * previous segment of that solve has finished, runs the
+ * tile and counts it done, so the solves advance independently inside one
+ * launch.  The host replays that launch in a CUDA graph once per iteration,
+ * tests every solve's residual (converged solves retire: their tiles are
+ * skipped) and confirms a stop on r - L phi as cc_solve does.  Every solver
+ * must be on one device with precision = 1, krylov = 0, fmg = 0,
+ * restriction = 0 and FP64 factors (else CC_ERR_INVALID_ARG); the iterates
+ * equal cc_solve's up to the order of the LU sweeps' atomic sums.  A wait that
+ * runs out ends the launch early and the call returns CC_ERR_TIMEOUT.
+ * Arguments as for cc_solve_batch; stats[i].ms_solve is the whole batch's time. */
+cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* const* f,
+                                    const double* const* g_box, const double* const* g_patch, double* const* phi,
+                                    int where, cc_stats* stats, cc_status* status);
 /* The same iteration for an already assembled r (grid array). */
 cc_status cc_solve_r(cc_solver* s, const double* r, double* phi, int where, cc_stats* stats);
 

@@ -88,6 +88,8 @@ SIGNATURES = {
     "cc_jacobi": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_solve_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                  C.POINTER(_P), C.c_int, _P, C.POINTER(C.c_int)]),
+    "cc_solve_batch_persistent": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                            C.POINTER(_P), C.c_int, _P, C.POINTER(C.c_int)]),
     "cc_lu_correction": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_lu_correction_static": (C.c_int, [_P, C.c_int, _P, _P]),
     "cc_restrict_residual": (C.c_int, [_P, C.c_int, _P, _P, _P]),
@@ -227,12 +229,15 @@ class Solver:
         cols = np.zeros(nnz, np.int32)
         vals = np.zeros(nnz)
         bptr = np.zeros(n2 + 1, np.int32)
-        # boundary terms: at most one per lattice cell
-        bpatch = np.zeros(nnz, np.int32)
-        bcoef = np.zeros(nnz)
+        # the boundary terms' count first (a lattice cell can carry a patch term
+        # and up to three box-face terms), then all arrays at their sizes
+        self._check(lib().cc_phi2_rows(self._h, level, None, None, None, None, _ptr(bptr), None, None),
+                    "cc_phi2_rows")
+        nb = int(bptr[-1])
+        bpatch = np.zeros(max(nb, 1), np.int32)
+        bcoef = np.zeros(max(nb, 1))
         self._check(lib().cc_phi2_rows(self._h, level, _ptr(cells), _ptr(ptr), _ptr(cols), _ptr(vals), _ptr(bptr),
                                        _ptr(bpatch), _ptr(bcoef)), "cc_phi2_rows")
-        nb = int(bptr[-1])
         return cells, ptr, cols, vals, bptr, bpatch[:nb], bcoef[:nb]
 
     # ---------------------------------------------------------------- data
@@ -350,9 +355,10 @@ class Solver:
         return out
 
 
-def solve_batch(solvers, fs, g_boxes, g_patches, phis, where=None):
-    """cc_solve_batch: solve i is solvers[i] with fs[i], g_boxes[i], g_patches[i]
-    and phis[i] (overwritten), all on the device (CUDA tensors) or all on the host.
+def solve_batch(solvers, fs, g_boxes, g_patches, phis, where=None, persistent=False):
+    """cc_solve_batch (persistent=True: cc_solve_batch_persistent): solve i is
+    solvers[i] with fs[i], g_boxes[i], g_patches[i] and phis[i] (overwritten),
+    all on the device (CUDA tensors) or all on the host.
     Returns (overall status, [cc_stats], [status])."""
     nb = len(solvers)
     if where is None:
@@ -361,8 +367,8 @@ def solve_batch(solvers, fs, g_boxes, g_patches, phis, where=None):
     hs = (_P * nb)(*[S._h for S in solvers])
     stats = (cc_stats * nb)()
     status = (C.c_int * nb)()
-    rc = lib().cc_solve_batch(hs, nb, arr(fs), arr(g_boxes), arr(g_patches), arr(phis), where,
-                              C.cast(stats, _P), status)
+    fn = lib().cc_solve_batch_persistent if persistent else lib().cc_solve_batch
+    rc = fn(hs, nb, arr(fs), arr(g_boxes), arr(g_patches), arr(phis), where, C.cast(stats, _P), status)
     return rc, list(stats), list(status)
 
 

@@ -110,7 +110,7 @@ __device__ __forceinline__ T interior13(T c0, T ip1, T im1, T jp1, T jm1, T kp1,
 // (L phi)_i for a phi1 cell (T = double: FP64 arithmetic; T = float: FP32); phi
 // may be stored in a narrower type S (FP32 values evaluated in FP64).
 template <class T, class S = T>
-__device__ __forceinline__ T apply_regular(const S* __restrict__ phi, int i, int j, int k, const StencilP& P) {
+__device__ __forceinline__ T apply_regular(const S* phi, int i, int j, int k, const StencilP& P) {
   // 32-bit indices: cc_setup limits n to 1024, so n^3 < 2^31
   const int n = P.n;
   const int nn = n * n;
@@ -153,14 +153,14 @@ template <> struct Vec2<double> { using type = double2; };
 // (k, j) tile of one plane (the tile shape is tuned per level at set-up);
 // interior pairs read their 13-point neighbourhoods as 2-element vector loads
 // (11 loads for two cells), pairs near the box take apply_regular.
+// The pair (k, k+1) of row (i, j) (k even); nothing outside the grid.  Its
+// pointers carry no __restrict__: the persistent batch kernel calls it on
+// arrays other blocks of the same launch wrote.
 template <class T>
-__global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
-                                               T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
-                                               StencilP P) {
+__device__ __forceinline__ void jacobi_pair(const T* phi_in, const T* s, T* phi_out, const uint8_t* typ,
+                                            const StencilP& P, int i, int j, int k) {
   using V2 = typename Vec2<T>::type;
   const int n = P.n;
-  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int i = blockIdx.z;
   if (k >= n || j >= n) return;
   const int nn = n * n;
   const int idx = (i * n + j) * n + k;  // even: n is even
@@ -196,6 +196,14 @@ __global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, co
     }
   }
   *reinterpret_cast<V2*>(phi_out + idx) = res;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, const T* __restrict__ s,
+                                               T* __restrict__ phi_out, const uint8_t* __restrict__ typ,
+                                               StencilP P) {
+  jacobi_pair<T>(phi_in, s, phi_out, typ, P, blockIdx.z, blockIdx.y * blockDim.y + threadIdx.y,
+                 2 * (blockIdx.x * blockDim.x + threadIdx.x));
 }
 
 // The interior row, exactly, for values held in FP32.  An FP32 value is
@@ -277,11 +285,10 @@ __device__ __forceinline__ double fx_scale(double f, int emax) {
 // k_resid1_z32_shell over the n^3 - (n-4)^3 cells nearer the box (FP64).  A warp
 // mixing the two would issue the FP64 path, at the FP64 pipe's rate, for its
 // few box lanes.
-__global__ void k_resid1_z32_in(const float* __restrict__ z, const double* __restrict__ s, double* __restrict__ out,
-                                const uint8_t* __restrict__ typ, StencilP P) {
+// One cell (i, j, k), all three at least 2 from the box, of k_resid1_z32_in.
+__device__ __forceinline__ void resid_z32_in_cell(const float* z, const double* s, double* out, const uint8_t* typ,
+                                                  const StencilP& P, int i, int j, int k) {
   const int n = P.n;
-  const int k = 2 + blockIdx.x * blockDim.x + threadIdx.x, j = 2 + blockIdx.y, i = 2 + blockIdx.z;
-  if (k >= n - 2) return;
   const int nn = n * n;
   const int idx = (i * n + j) * n + k;
   double r = 0.0;
@@ -299,6 +306,13 @@ __global__ void k_resid1_z32_in(const float* __restrict__ z, const double* __res
       r = s ? __fma_rn(acc, neg, s[idx]) : acc * neg;
   }
   out[idx] = r;
+}
+
+__global__ void k_resid1_z32_in(const float* __restrict__ z, const double* __restrict__ s, double* __restrict__ out,
+                                const uint8_t* __restrict__ typ, StencilP P) {
+  const int k = 2 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.n - 2) return;
+  resid_z32_in_cell(z, s, out, typ, P, 2 + blockIdx.z, 2 + blockIdx.y, k);
 }
 
 // The t-th cell within two cells of the box (n >= 4): the planes i in {0,1,n-2,n-1},
@@ -328,15 +342,20 @@ __device__ __forceinline__ void shell_cell(int t, int n, int& i, int& j, int& k)
   }
 }
 
+// The t-th cell within two cells of the box: its row in FP64.
+__device__ __forceinline__ void resid_z32_shell_cell(const float* z, const double* s, double* out,
+                                                     const uint8_t* typ, const StencilP& P, int t) {
+  const int n = P.n;
+  int i, j, k;
+  shell_cell(t, n, i, j, k);
+  const int idx = (i * n + j) * n + k;
+  out[idx] = typ[idx] == 1 ? (s ? s[idx] : 0.0) - apply_regular<double, float>(z, i, j, k, P) : 0.0;
+}
+
 __global__ void k_resid1_z32_shell(const float* __restrict__ z, const double* __restrict__ s,
                                    double* __restrict__ out, const uint8_t* __restrict__ typ, StencilP P, int count) {
-  const int n = P.n;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-    int i, j, k;
-    shell_cell(t, n, i, j, k);
-    const int idx = (i * n + j) * n + k;
-    out[idx] = typ[idx] == 1 ? (s ? s[idx] : 0.0) - apply_regular<double, float>(z, i, j, k, P) : 0.0;
-  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+    resid_z32_shell_cell(z, s, out, typ, P, t);
 }
 
 __global__ void k_resid1(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
@@ -356,15 +375,22 @@ __global__ void k_resid1(const double* __restrict__ phi, const double* __restric
   }
 }
 
+// Row r of the phi2 rows: out = s - (L phi) at its cell; returns the value.
+__device__ __forceinline__ double resid2_row(const double* phi, const double* s, double* out, const int* cell,
+                                             const int* ptr, const int* col, const double* val, int r) {
+  double v = s[cell[r]];
+  for (int p = ptr[r]; p < ptr[r + 1]; ++p) v -= val[p] * phi[col[p]];
+  out[cell[r]] = v;
+  return v;
+}
+
 // s - L phi on the phi2 rows (PLG rows), optionally accumulating ||.||^2
 __global__ void k_resid2(const double* __restrict__ phi, const double* __restrict__ s, double* __restrict__ out,
                          int n2, const int* __restrict__ cell, const int* __restrict__ ptr,
                          const int* __restrict__ col, const double* __restrict__ val, double* __restrict__ norm2) {
   double acc = 0.0;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n2; r += gridDim.x * blockDim.x) {
-    double v = s[cell[r]];
-    for (int p = ptr[r]; p < ptr[r + 1]; ++p) v -= val[p] * phi[col[p]];
-    out[cell[r]] = v;
+    const double v = resid2_row(phi, s, out, cell, ptr, col, val, r);
     acc += v * v;
   }
   if (norm2) {
@@ -375,11 +401,9 @@ __global__ void k_resid2(const double* __restrict__ phi, const double* __restric
 
 // coarse[I] = 2^-3 sum over the phi1 children of (s - L phi); 3-D launch over coarse cells
 template <class T>
-__global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T* __restrict__ coarse,
-                           const uint8_t* __restrict__ typ, StencilP P) {
+__device__ __forceinline__ void restrict_cell(const T* phi, const T* s, T* coarse, const uint8_t* typ,
+                                              const StencilP& P, int a, int b, int c) {
   const int n = P.n, nc = n / 2;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y, a = blockIdx.z;
-  if (c >= nc) return;
   T acc = 0;
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
@@ -388,6 +412,14 @@ __global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T
     if (typ[idx] == 1) acc += s[idx] - apply_regular<T>(phi, i, j, k, P);
   }
   coarse[(a * nc + b) * nc + c] = T(0.125) * acc;
+}
+
+template <class T>
+__global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ s, T* __restrict__ coarse,
+                           const uint8_t* __restrict__ typ, StencilP P) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.n / 2) return;
+  restrict_cell<T>(phi, s, coarse, typ, P, blockIdx.z, blockIdx.y, c);
 }
 
 // Full-weighting restriction, an option beside the paper's 2^-3 sum: the
@@ -433,15 +465,21 @@ __global__ void k_restrict_fw(const T* __restrict__ r, T* __restrict__ coarse, i
 // phi1 cells += the parent's correction, taken only from parents that are phi1
 // cells of the coarse level (a coarse phi2 cell prolongates no correction).
 template <class T>
-__global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
-                          const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
+__device__ __forceinline__ void prolong_pc_cell(const T* coarse, T* phi, const uint8_t* typ, const uint8_t* typ_c,
+                                                int n, int into_phi2, int i, int j, int k) {
   const int nc = n / 2;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= n) return;
   const int idx = (i * n + j) * n + k;
   if (typ[idx] != 1 && !(into_phi2 && typ[idx] == 2)) return;
   const int I = ((i >> 1) * nc + (j >> 1)) * nc + (k >> 1);
   if (typ_c[I] != 0) phi[idx] += coarse[I];
+}
+
+template <class T>
+__global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
+                          const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  prolong_pc_cell<T>(coarse, phi, typ, typ_c, n, into_phi2, blockIdx.z, blockIdx.y, k);
 }
 
 // Trilinear (cell-centred) prolongation, an option beside the paper's piecewise-
@@ -449,11 +487,9 @@ __global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ phi, con
 // its 8 nearest coarse cell centres, using only coarse phi1 cells and
 // renormalising the weights over those (so constants are prolongated exactly).
 template <class T>
-__global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
-                              const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
+__device__ __forceinline__ void prolong_tri_cell(const T* coarse, T* phi, const uint8_t* typ, const uint8_t* typ_c,
+                                                 int n, int into_phi2, int i, int j, int k) {
   const int nc = n / 2;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= n) return;
   const int idx = (i * n + j) * n + k;
   if (typ[idx] != 1 && !(into_phi2 && typ[idx] == 2)) return;
   const int I = i >> 1, J = j >> 1, K = k >> 1;
@@ -487,6 +523,14 @@ __global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi,
     phi[idx] += acc / wsum;
 }
 
+template <class T>
+__global__ void k_prolong_tri(const T* __restrict__ coarse, T* __restrict__ phi, const uint8_t* __restrict__ typ,
+                              const uint8_t* __restrict__ typ_c, int n, int into_phi2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  prolong_tri_cell<T>(coarse, phi, typ, typ_c, n, into_phi2, blockIdx.z, blockIdx.y, k);
+}
+
 constexpr int kBarGroups = 16;  // group counters of the one-launch sweeps' grid barrier (after one top counter)
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with
@@ -504,17 +548,22 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // The PLG rows are applied in FP64 (k_lu_rhs_df below serves the FP32 grids
 // whose factors are FP32 too); b is stored in the LU work type TW.  (x, the backward sweep's accumulator, is cleared here too.)
 template <class T, class TW>
+__device__ __forceinline__ void lu_rhs_row(TW* b, TW* x, const int* cell, const int* ptr, const int* col,
+                                           const double* val, const T* s, const T* phi, int p) {
+  double v = (double)s[cell[p]];
+  for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
+  b[p] = (TW)v;
+  x[p] = TW(0);
+}
+
+template <class T, class TW>
 __global__ void k_lu_rhs(TW* __restrict__ b, TW* __restrict__ x, int np, const int* __restrict__ cell,
                          const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
                          const T* __restrict__ s, const T* __restrict__ phi, unsigned int* __restrict__ bar) {
   pdl_trigger();  // the first sweep launch may be scheduled; it waits for this grid
   if (bar && blockIdx.x == 0 && threadIdx.x <= kBarGroups) bar[threadIdx.x] = 0u;  // one-launch sweep counters
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    double v = (double)s[cell[p]];
-    for (int q = ptr[p]; q < ptr[p + 1]; ++q) v -= val[q] * (double)phi[col[q]];
-    b[p] = (TW)v;
-    x[p] = TW(0);
-  }
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+    lu_rhs_row<T, TW>(b, x, cell, ptr, col, val, s, phi, p);
 }
 
 // The same for an FP32 grid with no FP64 arithmetic: the row is summed in
@@ -1060,6 +1109,236 @@ template <> double* DevLevel::btmp<double>() { return tmp; }
 template <> float* DevLevel::bs<float>() { return s32; }
 template <> float* DevLevel::be<float>() { return e32; }
 template <> float* DevLevel::btmp<float>() { return tmp32; }
+
+// ---- one V-cycle of many independent solves in one persistent launch
+// The host lists, per solve, the steps of one mixed-precision iteration (the
+// V-cycle of vcycle_rec<float> with FP64 LU-corrections, then the update of phi
+// and the recursive residual) as segments of tiles; the segments of all solves
+// are interleaved (step k of every solve, then step k+1) and numbered by a
+// running ticket.  Each block takes the next ticket from one global counter,
+// waits until the solve's previous segment has finished all its tiles, runs
+// its tile and counts it done.  A waiting block only ever waits for tickets
+// taken before its own, by blocks already running, so the launch always
+// progresses, with any grid size; every wait is bounded (error flag, then the
+// remaining tiles are skipped and the launch ends).
+constexpr int kBatchLevels = 16;
+constexpr int kBatchElems = 2048;  // cells of one tile of the elementwise steps (8 per thread)
+
+struct BLevel {
+  StencilP P;
+  int n = 0, jbx = 16, jby = 16;  // SMO-1 tile of 256 threads: 2 jbx cells along k x jby rows along j
+  long long N = 0;
+  const uint8_t* typ = nullptr;
+  float *s32 = nullptr, *e32 = nullptr, *tmp32 = nullptr;
+  int np = 0;  // LU-correction (bottom: direct solve) rows
+  const int *cell = nullptr, *rptr = nullptr, *rcol = nullptr, *structs = nullptr;
+  const double *rval = nullptr, *vals = nullptr;
+  double *b = nullptr, *x = nullptr;
+  const Task* tasks = nullptr;
+};
+
+struct BSolve {
+  BLevel lev[kBatchLevels];
+  int nlev = 0, n2 = 0, prolong = 1;
+  double *phi = nullptr, *s0 = nullptr, *e64 = nullptr, *s = nullptr;
+  const int *p2_cell = nullptr, *p2_ptr = nullptr, *p2_col = nullptr;
+  const double* p2_val = nullptr;
+};
+
+enum BOp : int {
+  B_TOFLOAT,  // level 0: s32 = (float) s0, e32 = 0
+  B_ZERO,     // e32 = 0
+  B_JAC,      // SMO-1: buffer a -> buffer b
+  B_LURHS,    // LU right-hand side from buffer a
+  B_SWEEPF,   // forward sweep, tasks [first, first + count)
+  B_SWEEPB,   // backward sweep
+  B_SCATTER,  // LU solution into buffer a
+  B_RESTRICT, // residual of buffer a -> s32 of the next level
+  B_PROLONG,  // e32 of the next level -> buffer a
+  B_COPY,     // e32 = tmp32
+  B_PHIUP,    // level 0: phi += e32, e64 = e32
+  B_RES_IN,   // level 0: s = s0 - L e32 on cells two or more from the box (exact fixed point)
+  B_RES_SHELL,// the same on the cells nearer the box (FP64)
+  B_RES2,     // the same on the phi2 rows, from e64
+  B_NORM      // s0 = s, norms[solve] += ||s||^2
+};
+
+struct BSeg {
+  long long t0 = 0;  // first ticket
+  long long first = 0;
+  int ntiles = 0, solve = 0, prev = -1, op = 0, lev = 0, a = 0, b = 0, count = 0;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ void batch_tile(const BSolve& S, const BSeg& g, int tile, double* norms) {
+  const BLevel& L = S.lev[g.lev];
+  const int tid = threadIdx.x;
+  float* const cur = g.a ? L.tmp32 : L.e32;
+  switch (g.op) {
+    case B_TOFLOAT:
+    case B_ZERO:
+    case B_COPY:
+    case B_PHIUP:
+      for (int u = 0; u < kBatchElems / 256; ++u) {
+        const long long q = (long long)tile * kBatchElems + u * 256 + tid;
+        if (q >= L.N) break;
+        if (g.op == B_TOFLOAT) {
+          L.s32[q] = (float)S.s0[q];
+          L.e32[q] = 0.0f;
+        } else if (g.op == B_ZERO) {
+          L.e32[q] = 0.0f;
+        } else if (g.op == B_COPY) {
+          L.e32[q] = L.tmp32[q];
+        } else {
+          const double e = (double)L.e32[q];
+          S.phi[q] += e;
+          S.e64[q] = e;
+        }
+      }
+      break;
+    case B_NORM: {
+      double acc = 0.0;
+      for (int u = 0; u < kBatchElems / 256; ++u) {
+        const long long q = (long long)tile * kBatchElems + u * 256 + tid;
+        if (q >= L.N) break;
+        const double v = S.s[q];
+        S.s0[q] = v;
+        acc += v * v;
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((tid & 31) == 0 && acc != 0.0) atomicAdd(norms + g.solve, acc);
+      break;
+    }
+    case B_JAC: {
+      const int gx = (L.n + 2 * L.jbx - 1) / (2 * L.jbx), gy = (L.n + L.jby - 1) / L.jby;
+      const int bx = tile % gx, r = tile / gx, by = r % gy, bz = r / gy;
+      const int tx = tid % L.jbx, ty = tid / L.jbx;
+      jacobi_pair<float>(cur, L.s32, g.b ? L.tmp32 : L.e32, L.typ, L.P, bz, by * L.jby + ty, 2 * (bx * L.jbx + tx));
+      break;
+    }
+    case B_LURHS: {
+      const int p = tile * 256 + tid;
+      if (p < L.np) lu_rhs_row<float, double>(L.b, L.x, L.cell, L.rptr, L.rcol, L.rval, L.s32, cur, p);
+      break;
+    }
+    case B_SWEEPF:
+    case B_SWEEPB: {
+      const long long t = g.first + (long long)tile * 8 + (tid >> 5);
+      if (t < g.first + g.count) {
+        if (g.op == B_SWEEPF)
+          run_tile<true, double>(L.tasks[t], tid & 31, L.vals, L.structs, L.b, L.x);
+        else
+          run_tile<false, double>(L.tasks[t], tid & 31, L.vals, L.structs, L.b, L.x);
+      }
+      break;
+    }
+    case B_SCATTER: {
+      const int p = tile * 256 + tid;
+      if (p < L.np) cur[L.cell[p]] = (float)__ldcg(L.x + p);
+      break;
+    }
+    case B_RESTRICT: {
+      const int nc = L.n / 2;
+      const int q = tile * 256 + tid;
+      if (q < nc * nc * nc)
+        restrict_cell<float>(cur, L.s32, S.lev[g.lev + 1].s32, L.typ, L.P, q / (nc * nc), (q / nc) % nc, q % nc);
+      break;
+    }
+    case B_PROLONG: {
+      const int n = L.n;
+      const int q = tile * 256 + tid;
+      if (q < n * n * n) {
+        const BLevel& C = S.lev[g.lev + 1];
+        if (S.prolong == 1)
+          prolong_tri_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, q / (n * n), (q / n) % n, q % n);
+        else
+          prolong_pc_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, q / (n * n), (q / n) % n, q % n);
+      }
+      break;
+    }
+    case B_RES_IN: {
+      const int m = L.n - 4;
+      const int q = tile * 256 + tid;
+      if (q < m * m * m) resid_z32_in_cell(L.e32, S.s0, S.s, L.typ, L.P, 2 + q / (m * m), 2 + (q / m) % m, 2 + q % m);
+      break;
+    }
+    case B_RES_SHELL: {
+      const int q = tile * 256 + tid;
+      if (q < g.count) resid_z32_shell_cell(L.e32, S.s0, S.s, L.typ, L.P, q);
+      break;
+    }
+    case B_RES2: {
+      const int r = tile * 256 + tid;
+      if (r < S.n2) resid2_row(S.e64, S.s0, S.s, S.p2_cell, S.p2_ptr, S.p2_col, S.p2_val, r);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_batch_cycle(const BSolve* __restrict__ sol, const BSeg* __restrict__ seg, int nseg, long long nticket,
+                  unsigned long long* ticket, unsigned int* done, const int* __restrict__ active, double* norms,
+                  unsigned int* err, long long spin_limit) {
+  __shared__ long long s_t;
+  __shared__ int s_seg, s_go;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long t = (long long)atomicAdd(ticket, 1ull);
+      int si = -1, go = 0;
+      if (t < nticket) {
+        int lo = 0, hi = nseg - 1;  // the last segment with t0 <= t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (seg[mid].t0 <= t)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        si = lo;
+        const BSeg& g = seg[si];
+        go = active[g.solve] && *(volatile unsigned int*)err == 0u;
+        if (go && g.prev >= 0) {
+          const unsigned int need = (unsigned int)seg[g.prev].ntiles;
+          long long spins = 0;
+          while (ld_acquire(done + g.prev) < need) {
+            if (*(volatile unsigned int*)err) {
+              go = 0;
+              break;
+            }
+            if (++spins > spin_limit) {
+              atomicExch(err, 1u);
+              go = 0;
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+      }
+      s_t = t;
+      s_seg = si;
+      s_go = go;
+    }
+    __syncthreads();
+    const long long t = s_t;
+    const int si = s_seg, go = s_go;
+    __syncthreads();
+    if (si < 0) break;
+    if (go) batch_tile(sol[seg[si].solve], seg[si], (int)(t - seg[si].t0), norms);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(done + si, 1u);
+    }
+  }
+}
 
 enum Prof {
   P_JACOBI,
@@ -2224,6 +2503,122 @@ cc_status static_scratch(cc_solver* S, double** out) {
 
 thread_local std::string g_setup_err;  // message of the last failed cc_setup on this thread
 
+// ------------------------------------------ batched solves, one persistent launch per V-cycle
+namespace {
+
+struct BatchBuild {
+  std::vector<BSeg> segs;
+  void push(int op, int lev, long long ntiles, int a = 0, int b = 0, long long first = 0, int count = 0) {
+    if (ntiles <= 0) return;
+    BSeg g;
+    g.op = op;
+    g.lev = lev;
+    g.ntiles = (int)ntiles;
+    g.a = a;
+    g.b = b;
+    g.first = first;
+    g.count = count;
+    segs.push_back(g);
+  }
+  // lu_solve_ws<float, double>: right-hand side, sweeps by height, scatter
+  void lu(const DevLU& D, int lev, int a) {
+    if (D.np == 0) return;
+    push(B_LURHS, lev, (D.np + 255) / 256, a);
+    for (int h = 0; h <= D.height; ++h) {
+      const long long f0 = D.toff[0][h], c = D.toff[0][h + 1] - f0;
+      push(B_SWEEPF, lev, (c + 7) / 8, 0, 0, f0, (int)c);
+    }
+    for (int h = D.height; h >= 0; --h) {
+      const long long f0 = D.toff[1][h], c = D.toff[1][h + 1] - f0;
+      push(B_SWEEPB, lev, (c + 7) / 8, 0, 0, f0, (int)c);
+    }
+    push(B_SCATTER, lev, (D.np + 255) / 256, a);
+  }
+  // vcycle_rec<float> on level m (e32 of level 0 is cleared by B_TOFLOAT)
+  void vcycle(const cc_solver* S, int m) {
+    const DevLevel& L = S->lev[m];
+    const int M = (int)S->lev.size() - 1;
+    if (m > 0) push(B_ZERO, m, (L.N + kBatchElems - 1) / kBatchElems);
+    if (m == M) {
+      lu(L.lu, m, 0);
+      return;
+    }
+    const int jbx = (int)L.jblock.x, jby = 256 / jbx;
+    const long long jt = (long long)((L.n + 2 * jbx - 1) / (2 * jbx)) * ((L.n + jby - 1) / jby) * L.n;
+    int cur = 0;
+    for (int it = 0; it < S->prm.nu1; ++it) {
+      push(B_JAC, m, jt, cur, 1 - cur);
+      cur = 1 - cur;
+      lu(L.lu, m, cur);
+    }
+    const long long nc = L.n / 2;
+    push(B_RESTRICT, m, (nc * nc * nc + 255) / 256, cur);
+    vcycle(S, m + 1);
+    push(B_PROLONG, m, (L.N + 255) / 256, cur);
+    for (int it = 0; it < S->prm.nu2; ++it) {
+      push(B_JAC, m, jt, cur, 1 - cur);
+      cur = 1 - cur;
+      lu(L.lu, m, cur);
+    }
+    if (cur != 0) push(B_COPY, m, (L.N + kBatchElems - 1) / kBatchElems);
+  }
+  // one_cycle with precision 1: the V-cycle, phi += e, the recursive residual and its norm
+  void iteration(const cc_solver* S) {
+    const DevLevel& L = S->lev[0];
+    push(B_TOFLOAT, 0, (L.N + kBatchElems - 1) / kBatchElems);
+    vcycle(S, 0);
+    push(B_PHIUP, 0, (L.N + kBatchElems - 1) / kBatchElems);
+    const long long m = L.n - 4, shell = L.N - m * m * m;
+    push(B_RES_IN, 0, (m * m * m + 255) / 256);
+    push(B_RES_SHELL, 0, (shell + 255) / 256, 0, 0, 0, (int)shell);
+    push(B_RES2, 0, (L.n2 + 255) / 256);
+    push(B_NORM, 0, (L.N + kBatchElems - 1) / kBatchElems);
+  }
+};
+
+BLevel blevel(const DevLevel& L) {
+  BLevel b;
+  b.P = L.P;
+  b.n = L.n;
+  b.jbx = (int)L.jblock.x;
+  b.jby = 256 / b.jbx;
+  b.N = L.N;
+  b.typ = L.typ;
+  b.s32 = L.s32;
+  b.e32 = L.e32;
+  b.tmp32 = L.tmp32;
+  b.np = L.lu.np;
+  b.cell = L.lu.cell;
+  b.rptr = L.lu.rptr;
+  b.rcol = L.lu.rcol;
+  b.structs = L.lu.structs;
+  b.rval = L.lu.rval;
+  b.vals = L.lu.vals;
+  b.b = L.lu.b;
+  b.x = L.lu.x;
+  b.tasks = L.lu.tasks;
+  return b;
+}
+
+// why the persistent batch cannot take solver S (nullptr: it can)
+const char* batch_unsupported(const cc_solver* S, int device) {
+  if (S->host_only) return "a solver was set up host-only";
+  if (S->device != device) return "all solvers of a batch must be on one device";
+  if (S->prm.precision != 1) return "the persistent batch runs precision 1 (FP32 V-cycle, FP64 LU-corrections)";
+  if (S->prm.krylov != 0 || S->prm.fmg != 0) return "the persistent batch runs Alg. Multigrid from the given guess";
+  if (S->prm.restriction != 0) return "the persistent batch uses the paper's restriction";
+  if ((int)S->lev.size() > kBatchLevels) return "too many levels";
+  for (size_t m = 0; m < S->lev.size(); ++m) {
+    const DevLevel& L = S->lev[m];
+    if (L.lu.f32 || L.lu.df) return "FP64 LU factors required";
+    if (m + 1 < S->lev.size() && (L.n % 2 || 256 % (int)L.jblock.x)) return "odd level or SMO-1 tile";
+  }
+  if (S->lev[0].n < 8) return "level 0 too small";
+  return nullptr;
+}
+
+}  // namespace
+
 extern "C" {
 
 void cc_default_params(cc_params* p) {
@@ -2772,6 +3167,225 @@ cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, co
   for (auto& th : pool) th.join();
   cc_status result = CC_OK;
   for (int i = 0; i < nb; ++i) {
+    if (status) status[i] = st[i];
+    if (result == CC_OK && st[i] != CC_OK) result = st[i];
+  }
+  return result;
+}
+
+cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* const* f,
+                                    const double* const* g_box, const double* const* g_patch, double* const* phi,
+                                    int where, cc_stats* stats, cc_status* status) {
+  if (nb < 0 || (nb > 0 && (!s || !f || !g_box || !g_patch || !phi))) return CC_ERR_INVALID_ARG;
+  if (nb == 0) return CC_OK;
+  for (int i = 0; i < nb; ++i)
+    if (!s[i] || !phi[i]) return CC_ERR_INVALID_ARG;
+  cc_solver* S = s[0];
+  for (int i = 0; i < nb; ++i)
+    if (const char* why = batch_unsupported(s[i], S->device)) return fail(S, CC_ERR_INVALID_ARG, why);
+  CK(cudaSetDevice(S->device));
+  std::vector<cc_status> st(nb, CC_OK);
+  std::vector<double> rn(nb, 0.0), rel(nb, 0.0), rel0(nb, 0.0);
+  std::vector<int> iters(nb, 0), live(nb, 1);
+  if (stats)
+    for (int i = 0; i < nb; ++i) std::memset(&stats[i], 0, sizeof(cc_stats));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, S->stream));
+  // data, guess, ||r|| and the first residual of every solve, on each solver's stream
+  for (int i = 0; i < nb; ++i) {
+    cc_solver* Si = s[i];
+    cc_status r = build_rhs(Si, f[i], g_box[i], g_patch[i], where);
+    if (r) return r;
+    DevLevel& L = Si->lev[0];
+    CK(cudaStreamWaitEvent(Si->stream, e0, 0));
+    CK(cudaMemcpyAsync(Si->phi, phi[i], L.N * sizeof(double),
+                       where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, Si->stream));
+    k_mask<<<grid_for(Si, L.N, 256), 256, 0, Si->stream>>>(Si->phi, L.typ, L.N);
+    CK(cudaMemsetAsync(Si->norm, 0, sizeof(double), Si->stream));
+    k_norm2<<<grid_for(Si, L.N, 256), 256, 0, Si->stream>>>(Si->r, L.N, Si->norm);
+    CK(cudaMemcpyAsync(Si->hnorm, Si->norm, sizeof(double), cudaMemcpyDeviceToHost, Si->stream));
+    CK(cudaStreamSynchronize(Si->stream));
+    rn[i] = std::sqrt(*Si->hnorm);
+    outer_residual(Si);
+  }
+  for (int i = 0; i < nb; ++i) {
+    CK(cudaStreamSynchronize(s[i]->stream));
+    rel[i] = rn[i] > 0 ? std::sqrt(*s[i]->hnorm) / rn[i] : 0.0;
+  }
+  // the segments of one iteration of every solve, interleaved step by step
+  std::vector<std::vector<BSeg>> prog(nb);
+  size_t longest = 0;
+  for (int i = 0; i < nb; ++i) {
+    BatchBuild bb;
+    bb.iteration(s[i]);
+    prog[i] = std::move(bb.segs);
+    longest = std::max(longest, prog[i].size());
+  }
+  std::vector<BSeg> segs;
+  std::vector<int> last(nb, -1);
+  long long nticket = 0;
+  for (size_t k = 0; k < longest; ++k)
+    for (int i = 0; i < nb; ++i) {
+      if (k >= prog[i].size()) continue;
+      BSeg g = prog[i][k];
+      g.solve = i;
+      g.prev = last[i];
+      g.t0 = nticket;
+      nticket += g.ntiles;
+      last[i] = (int)segs.size();
+      segs.push_back(g);
+    }
+  std::vector<BSolve> bs(nb);
+  for (int i = 0; i < nb; ++i) {
+    const cc_solver* Si = s[i];
+    BSolve& b = bs[i];
+    b.nlev = (int)Si->lev.size();
+    for (int m = 0; m < b.nlev; ++m) b.lev[m] = blevel(Si->lev[m]);
+    b.prolong = Si->prm.prolong;
+    const DevLevel& L = Si->lev[0];
+    b.n2 = L.n2;
+    b.phi = Si->phi;
+    b.s0 = Si->s0;
+    b.e64 = L.e;
+    b.s = L.s;
+    b.p2_cell = L.p2_cell;
+    b.p2_ptr = L.p2_ptr;
+    b.p2_col = L.p2_col;
+    b.p2_val = L.p2_val;
+  }
+  // device descriptors and counters, freed on every return below
+  struct Bufs {
+    BSolve* sol = nullptr;
+    BSeg* seg = nullptr;
+    unsigned int* done = nullptr;
+    unsigned long long* ticket = nullptr;
+    int* active = nullptr;
+    double* norms = nullptr;
+    unsigned int* err = nullptr;
+    int* hactive = nullptr;
+    double* hnorms = nullptr;
+    unsigned int* herr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~Bufs() {
+      if (exec) cudaGraphExecDestroy(exec);
+      cudaFree(sol);
+      cudaFree(seg);
+      cudaFree(done);
+      cudaFree(ticket);
+      cudaFree(active);
+      cudaFree(norms);
+      cudaFree(err);
+      if (hactive) cudaFreeHost(hactive);
+      if (hnorms) cudaFreeHost(hnorms);
+      if (herr) cudaFreeHost(herr);
+    }
+  } B;
+  const int nseg = (int)segs.size();
+  CK(cudaMalloc((void**)&B.sol, sizeof(BSolve) * nb));
+  CK(cudaMalloc((void**)&B.seg, sizeof(BSeg) * std::max(1, nseg)));
+  CK(cudaMalloc((void**)&B.done, sizeof(unsigned int) * std::max(1, nseg)));
+  CK(cudaMalloc((void**)&B.ticket, sizeof(unsigned long long)));
+  CK(cudaMalloc((void**)&B.active, sizeof(int) * nb));
+  CK(cudaMalloc((void**)&B.norms, sizeof(double) * nb));
+  CK(cudaMalloc((void**)&B.err, sizeof(unsigned int)));
+  CK(cudaMallocHost((void**)&B.hactive, sizeof(int) * nb));
+  CK(cudaMallocHost((void**)&B.hnorms, sizeof(double) * nb));
+  CK(cudaMallocHost((void**)&B.herr, sizeof(unsigned int)));
+  CK(cudaMemcpy(B.sol, bs.data(), sizeof(BSolve) * nb, cudaMemcpyHostToDevice));
+  if (nseg) CK(cudaMemcpy(B.seg, segs.data(), sizeof(BSeg) * nseg, cudaMemcpyHostToDevice));
+  CK(cudaMemset(B.err, 0, sizeof(unsigned int)));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle, 256, 0));
+  const int grid = std::max(1, per_sm) * S->nsm;
+  const long long spins = S->prm.lu_barrier_spins > 0 ? (long long)S->prm.lu_barrier_spins : kBarrierSpins;
+  // one iteration of every live solve: the active flags in, the counters cleared,
+  // the persistent launch, the residual norms and the error flag out
+  cudaStream_t q = S->stream;
+  {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(B.active, B.hactive, sizeof(int) * nb, cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(B.ticket, 0, sizeof(unsigned long long), q);
+    cudaMemsetAsync(B.done, 0, sizeof(unsigned int) * std::max(1, nseg), q);
+    cudaMemsetAsync(B.norms, 0, sizeof(double) * nb, q);
+    k_batch_cycle<<<grid, 256, 0, q>>>(B.sol, B.seg, nseg, nticket, B.ticket, B.done, B.active, B.norms, B.err,
+                                       spins);
+    cudaMemcpyAsync(B.hnorms, B.norms, sizeof(double) * nb, cudaMemcpyDeviceToHost, q);
+    cudaMemcpyAsync(B.herr, B.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, q);
+    CK(cudaStreamEndCapture(q, &g));
+    const cudaError_t ie = cudaGraphInstantiate(&B.exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+  }
+  cc_status result = CC_OK;
+  for (int it = 0;; ++it) {
+    // the convergence test of Alg. Multigrid for every live solve
+    int nlive = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (!live[i]) continue;
+      if (stats && iters[i] < 256) stats[i].resid_hist[iters[i]] = rel[i];
+      if (iters[i] == 0) rel0[i] = rel[i];
+      if (!std::isfinite(rel[i]) || (iters[i] > 0 && rel[i] > 1e4 * std::max(1.0, rel0[i]))) {
+        st[i] = CC_ERR_DIVERGED;
+        live[i] = 0;
+        continue;
+      }
+      if (rel[i] < s[i]->prm.rel_tol && iters[i] > 0) {  // confirm on r - L phi
+        outer_residual(s[i]);
+        CK(cudaStreamSynchronize(s[i]->stream));
+        rel[i] = rn[i] > 0 ? std::sqrt(*s[i]->hnorm) / rn[i] : 0.0;
+        if (stats && iters[i] < 256) stats[i].resid_hist[iters[i]] = rel[i];
+      }
+      if (rel[i] < s[i]->prm.rel_tol) {
+        live[i] = 0;
+        continue;
+      }
+      if (iters[i] >= s[i]->prm.max_iter) {
+        st[i] = CC_ERR_NOT_CONVERGED;
+        live[i] = 0;
+        continue;
+      }
+      ++nlive;
+    }
+    if (nlive == 0) break;
+    for (int i = 0; i < nb; ++i) B.hactive[i] = live[i];
+    CK(cudaGraphLaunch(B.exec, q));
+    CK(cudaStreamSynchronize(q));
+    if (*B.herr) {
+      result = fail(S, CC_ERR_TIMEOUT, "persistent batch: a segment wait ran out");
+      for (int i = 0; i < nb; ++i)
+        if (live[i]) st[i] = CC_ERR_TIMEOUT;
+      break;
+    }
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) {
+        ++iters[i];
+        rel[i] = rn[i] > 0 ? std::sqrt(B.hnorms[i]) / rn[i] : 0.0;
+      }
+  }
+  for (int i = 0; i < nb; ++i) {
+    cc_solver* Si = s[i];
+    DevLevel& L = Si->lev[0];
+    if (Si->nabs) k_absorbed<<<grid_for(Si, Si->nabs, 128), 128, 0, q>>>(Si->phi, Si->nabs, Si->a_cell, Si->a_own);
+    CK(cudaMemcpyAsync(phi[i], Si->phi, L.N * sizeof(double),
+                       where == CC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, q));
+  }
+  CK(cudaEventRecord(e1, q));
+  CK(cudaStreamSynchronize(q));
+  CK(cudaGetLastError());
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < nb; ++i) {
+    if (stats) {
+      stats[i].iters = iters[i];
+      stats[i].converged = st[i] == CC_OK && rel[i] < s[i]->prm.rel_tol;
+      stats[i].rel_resid = rel[i];
+      stats[i].ms_solve = ms;
+    }
     if (status) status[i] = st[i];
     if (result == CC_OK && st[i] != CC_OK) result = st[i];
   }

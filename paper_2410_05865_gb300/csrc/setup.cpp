@@ -52,30 +52,39 @@ constexpr int kCandMax = 64;
 
 // ----------------------------------------------------------- shift tables
 // (T m)[alpha] = sum_{beta<=alpha} prod_d C(alpha_d,beta_d) delta_d^(alpha_d-beta_d) m[beta]
+void shift_matrix(const int del[3], double* t) {
+  const Mono& M = mono();
+  static const double C[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  for (int k = 0; k < kNMono * kNMono; ++k) t[k] = 0.0;
+  for (int k = 0; k < kNMono; ++k) {
+    const int* a = M.e[k];
+    for (int i = 0; i <= a[0]; ++i)
+      for (int j = 0; j <= a[1]; ++j)
+        for (int l = 0; l <= a[2]; ++l) {
+          double v = C[a[0]][i] * C[a[1]][j] * C[a[2]][l] * std::pow((double)del[0], a[0] - i) *
+                     std::pow((double)del[1], a[1] - j) * std::pow((double)del[2], a[2] - l);
+          t[k * kNMono + M.idx[i][j][l]] = v;
+        }
+  }
+}
+
+constexpr int kShiftReach = 4;  // tabulated offsets: [-4, 4]^3
+
 struct ShiftTables {
   // delta in [-4,4]^3 -> 35x35 (first 20x20 block serves the degree-3 moments)
   std::vector<double> T;
   ShiftTables() : T(729 * kNMono * kNMono, 0.0) {
-    const Mono& M = mono();
-    static const double C[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
-    for (int dx = -4; dx <= 4; ++dx)
-      for (int dy = -4; dy <= 4; ++dy)
-        for (int dz = -4; dz <= 4; ++dz) {
-          double* t = &T[(((dx + 4) * 9 + (dy + 4)) * 9 + (dz + 4)) * kNMono * kNMono];
+    for (int dx = -kShiftReach; dx <= kShiftReach; ++dx)
+      for (int dy = -kShiftReach; dy <= kShiftReach; ++dy)
+        for (int dz = -kShiftReach; dz <= kShiftReach; ++dz) {
           const int del[3] = {dx, dy, dz};
-          for (int k = 0; k < kNMono; ++k) {
-            const int* a = M.e[k];
-            for (int i = 0; i <= a[0]; ++i)
-              for (int j = 0; j <= a[1]; ++j)
-                for (int l = 0; l <= a[2]; ++l) {
-                  double v = C[a[0]][i] * C[a[1]][j] * C[a[2]][l] * std::pow((double)del[0], a[0] - i) *
-                             std::pow((double)del[1], a[1] - j) * std::pow((double)del[2], a[2] - l);
-                  t[k * kNMono + M.idx[i][j][l]] = v;
-                }
-          }
+          shift_matrix(del, &T[(((dx + 4) * 9 + (dy + 4)) * 9 + (dz + 4)) * kNMono * kNMono]);
         }
   }
+  // nullptr for an offset outside the table
   const double* get(const int d[3]) const {
+    for (int a = 0; a < 3; ++a)
+      if (d[a] < -kShiftReach || d[a] > kShiftReach) return nullptr;
     return &T[(((d[0] + 4) * 9 + (d[1] + 4)) * 9 + (d[2] + 4)) * kNMono * kNMono];
   }
 };
@@ -86,8 +95,16 @@ const ShiftTables& shifts() {
 }
 
 // out[0..nm) = T(delta) * m, nm = 35 or 20 (degree <= 3 moments are a prefix).
+// A merged cell's parts can lie more than four cells from the unknown's cell
+// (the largest part owns it): those offsets build their matrix on the spot.
 void shift(const double* m, const int d[3], int nm, double* out) {
   const double* t = shifts().get(d);
+  std::vector<double> own;
+  if (!t) {
+    own.resize(kNMono * kNMono);
+    shift_matrix(d, own.data());
+    t = own.data();
+  }
   for (int k = 0; k < nm; ++k) {
     double s = 0;
     for (int j = 0; j < nm; ++j) s += t[k * kNMono + j] * m[j];

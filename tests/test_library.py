@@ -154,3 +154,49 @@ def test_host_lu_block_forms(host_pair):
         rel, pmin, pmax = S.lu_check(m)
         assert rel < 1e-12, (m, rel)
         assert pmin > 1e-14 * pmax
+
+
+def test_far_merged_parts_rows_exact(ccmg):
+    """A sphere of radius 0.46 at 32^3 leaves slivers of fluid between it and
+    the box walls; cell merging joins them into groups whose parts lie up to 9
+    cells from the unknown's cell (the largest part).  The moments of such a
+    group are its parts' moments shifted to that cell, and the phi2 rows built
+    from them must still be exact for polynomials of degree <= 4 (Sec. 4.1):
+    for p = x^2 + yz/2 - 0.3 x z^2 + 0.2 y^3, each finest-level row applied to
+    the merged cell averages of p, plus its boundary terms applied to the
+    Dirichlet data <<p>> and <p>, equals the merged cell average of Lap p.
+    The coarsest level's rows carry more boundary terms than entries (up to
+    three box faces per lattice cell), which phi2_rows must size for."""
+    import workloads as W
+    n = 32
+    prob = W.sphere_problem(n, radius=0.46)
+    S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=-1, min_coarse_n=8)
+    try:
+        P = lambda x, y, z: x * x + 0.5 * y * z - 0.3 * z * z * x + 0.2 * y ** 3
+        G = lambda x, y, z: (2 * x - 0.3 * z * z, 0.5 * z + 0.6 * y * y, 0.5 * y - 0.6 * z * x)
+        LAP = lambda x, y, z: 2.0 - 0.6 * x + 1.2 * y + 0 * z
+        kind, typ, owner, vol = S.cell_map(0)
+        idx = np.arange(n ** 3)
+        far = np.abs(np.stack(np.unravel_index(idx[owner >= 0], (n,) * 3))
+                     - np.stack(np.unravel_index(owner[owner >= 0], (n,) * 3))).max()
+        assert far > 4  # beyond the tabulated shifts
+        own = np.where(owner >= 0, owner, idx)
+        den = np.bincount(own, weights=vol, minlength=n ** 3)
+        safe = np.where(den > 0, den, 1.0)
+        pbar = np.bincount(own, weights=ccmg.cell_averages(S, P) * vol, minlength=n ** 3) / safe
+        lbar = np.bincount(own, weights=ccmg.cell_averages(S, LAP) * vol, minlength=n ** 3) / safe
+        gb = ccmg.box_face_averages(S, P, G, prob.box_bc)
+        gp = ccmg.patch_averages(S, P, G, prob.shape_bc)
+        cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(0)
+        for r, c in enumerate(cells):
+            lhs = np.dot(vals[ptr[r]:ptr[r + 1]], pbar[cols[ptr[r]:ptr[r + 1]]])
+            for q in range(bptr[r], bptr[r + 1]):
+                b = bpatch[q]
+                lhs += bcoef[q] * (gp[b] if b >= 0 else gb[-1 - b])
+            scale = np.abs(vals[ptr[r]:ptr[r + 1]]).max() * np.abs(pbar).max()
+            assert abs(lhs - lbar[c]) < 1e-11 * scale, r
+        m = S.info.n_levels - 1
+        cells, ptr, cols, vals, bptr, bpatch, bcoef = S.phi2_rows(m)
+        assert bptr[-1] > S.info.phi2_nnz[m] and len(bpatch) == bptr[-1]
+    finally:
+        S.close()

@@ -234,19 +234,19 @@ cc_status cc_solve_batch(cc_solver* const* s, int nb, const double* const* f, co
  * precision-1 V-cycle of cc_solve: SMO-1, LU-corrections by tree height,
  * restriction, bottom solve, prolongation; then phi += e and the recursive
  * residual s -= L e with its norm) is listed as a chain of segments, each a
- * set of tiles (a block of cells, rows or eight LU warp tiles); the segments
- * of all solves are interleaved step by step and numbered by a running ticket.
- * Each block of the launch takes the next ticket, waits (at most the first
- * solver's params.lu_barrier_spins polls, by default about a second) until the
- * previous segment of that solve has finished, runs the
- * tile and counts it done, so the solves advance independently inside one
- * launch.  The host replays that launch in a CUDA graph once per iteration,
- * tests every solve's residual (converged solves retire: their tiles are
- * skipped) and confirms a stop on r - L phi as cc_solve does.  Every solver
- * must be on one device with precision = 1, krylov = 0, fmg = 0,
- * restriction = 0 and FP64 factors (else CC_ERR_INVALID_ARG); the iterates
- * equal cc_solve's up to the order of the LU sweeps' atomic sums.  A wait that
- * runs out ends the launch early and the call returns CC_ERR_TIMEOUT.
+ * set of tiles (a block of cells, rows or eight LU warp tiles).  Each solve has
+ * a claim word (its current segment and the tiles handed out); the blocks of
+ * the launch claim tiles of any solve whose current segment has some left, and
+ * the block finishing a segment's last tile moves that solve on, so the solves
+ * advance independently inside one launch.  The host replays that launch in a
+ * CUDA graph once per iteration, tests every solve's residual (converged
+ * solves retire: their chains are skipped) and confirms a stop on r - L phi
+ * as cc_solve does.  Every solver must be on one device with precision = 1,
+ * krylov = 0, fmg = 0, restriction = 0 and FP64 factors (else
+ * CC_ERR_INVALID_ARG); the iterates equal cc_solve's up to the order of the LU
+ * sweeps' atomic sums.  A block finding no work polls again at most the first
+ * solver's params.lu_barrier_spins times in a row (default about a second);
+ * past that the launch ends early and the call returns CC_ERR_TIMEOUT.
  * Arguments as for cc_solve_batch; stats[i].ms_solve is the whole batch's time. */
 cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* const* f,
                                     const double* const* g_box, const double* const* g_patch, double* const* phi,

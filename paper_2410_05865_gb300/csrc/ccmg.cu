@@ -1113,16 +1113,16 @@ template <> float* DevLevel::btmp<float>() { return tmp32; }
 // ---- one V-cycle of many independent solves in one persistent launch
 // The host lists, per solve, the steps of one mixed-precision iteration (the
 // V-cycle of vcycle_rec<float> with FP64 LU-corrections, then the update of phi
-// and the recursive residual) as segments of tiles; the segments of all solves
-// are interleaved (step k of every solve, then step k+1) and numbered by a
-// running ticket.  Each block takes the next ticket from one global counter,
-// waits until the solve's previous segment has finished all its tiles, runs
-// its tile and counts it done.  A waiting block only ever waits for tickets
-// taken before its own, by blocks already running, so the launch always
-// progresses, with any grid size; every wait is bounded (error flag, then the
-// remaining tiles are skipped and the launch ends).
+// and the recursive residual) as a chain of segments, each a set of tiles.
+// Every solve has one claim word, (current segment << 32) | tiles claimed.  A
+// block looks over the solves (from a rotating start) for one whose current
+// segment still has unclaimed tiles, claims one by compare-and-swap, runs it
+// and counts it done; the block that finishes a segment's last tile moves the
+// solve to its next segment.  So the solves advance independently and a block
+// never waits on one solve while another has work.  A block finding no work
+// polls again, at most spin_limit times in a row (error flag, then every block
+// returns); a launch ends when every solve has run its chain.
 constexpr int kBatchLevels = 16;
-constexpr int kBatchElems = 2048;  // cells of one tile of the elementwise steps (8 per thread)
 
 struct BLevel {
   StencilP P;
@@ -1164,28 +1164,22 @@ enum BOp : int {
 };
 
 struct BSeg {
-  long long t0 = 0;  // first ticket
-  long long first = 0;
-  int ntiles = 0, solve = 0, prev = -1, op = 0, lev = 0, a = 0, b = 0, count = 0;
+  long long first = 0;  // sweeps: first task
+  int ntiles = 0, per = 0, op = 0, lev = 0, a = 0, b = 0, count = 0;  // per: items of one tile
 };
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ void batch_tile(const BSolve& S, const BSeg& g, int tile, double* norms) {
+__device__ void batch_tile(const BSolve& S, int solve, const BSeg& g, int tile, double* norms) {
   const BLevel& L = S.lev[g.lev];
   const int tid = threadIdx.x;
   float* const cur = g.a ? L.tmp32 : L.e32;
+  const long long q0 = (long long)tile * g.per;  // first item of the tile (g.per items, a multiple of 256)
   switch (g.op) {
     case B_TOFLOAT:
     case B_ZERO:
     case B_COPY:
     case B_PHIUP:
-      for (int u = 0; u < kBatchElems / 256; ++u) {
-        const long long q = (long long)tile * kBatchElems + u * 256 + tid;
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
         if (q >= L.N) break;
         if (g.op == B_TOFLOAT) {
           L.s32[q] = (float)S.s0[q];
@@ -1203,139 +1197,195 @@ __device__ void batch_tile(const BSolve& S, const BSeg& g, int tile, double* nor
       break;
     case B_NORM: {
       double acc = 0.0;
-      for (int u = 0; u < kBatchElems / 256; ++u) {
-        const long long q = (long long)tile * kBatchElems + u * 256 + tid;
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
         if (q >= L.N) break;
         const double v = S.s[q];
         S.s0[q] = v;
         acc += v * v;
       }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0 && acc != 0.0) atomicAdd(norms + g.solve, acc);
+      if ((tid & 31) == 0 && acc != 0.0) atomicAdd(norms + solve, acc);
       break;
     }
-    case B_JAC: {
+    case B_JAC: {  // g.per grid planes of one (2 jbx) x jby tile of (k, j)
       const int gx = (L.n + 2 * L.jbx - 1) / (2 * L.jbx), gy = (L.n + L.jby - 1) / L.jby;
       const int bx = tile % gx, r = tile / gx, by = r % gy, bz = r / gy;
       const int tx = tid % L.jbx, ty = tid / L.jbx;
-      jacobi_pair<float>(cur, L.s32, g.b ? L.tmp32 : L.e32, L.typ, L.P, bz, by * L.jby + ty, 2 * (bx * L.jbx + tx));
+      for (int u = 0; u < g.per; ++u) {
+        const int i = bz * g.per + u;
+        if (i >= L.n) break;
+        jacobi_pair<float>(cur, L.s32, g.b ? L.tmp32 : L.e32, L.typ, L.P, i, by * L.jby + ty, 2 * (bx * L.jbx + tx));
+      }
       break;
     }
-    case B_LURHS: {
-      const int p = tile * 256 + tid;
-      if (p < L.np) lu_rhs_row<float, double>(L.b, L.x, L.cell, L.rptr, L.rcol, L.rval, L.s32, cur, p);
+    case B_LURHS:
+      for (int u = tid; u < g.per; u += 256) {
+        const long long p = q0 + u;
+        if (p < L.np) lu_rhs_row<float, double>(L.b, L.x, L.cell, L.rptr, L.rcol, L.rval, L.s32, cur, (int)p);
+      }
       break;
-    }
     case B_SWEEPF:
-    case B_SWEEPB: {
-      const long long t = g.first + (long long)tile * 8 + (tid >> 5);
-      if (t < g.first + g.count) {
+    case B_SWEEPB:  // g.per warp tiles, a multiple of 8
+      for (int u = tid >> 5; u < g.per; u += 8) {
+        const long long t = g.first + q0 + u;
+        if (t >= g.first + g.count) break;
         if (g.op == B_SWEEPF)
           run_tile<true, double>(L.tasks[t], tid & 31, L.vals, L.structs, L.b, L.x);
         else
           run_tile<false, double>(L.tasks[t], tid & 31, L.vals, L.structs, L.b, L.x);
       }
       break;
-    }
-    case B_SCATTER: {
-      const int p = tile * 256 + tid;
-      if (p < L.np) cur[L.cell[p]] = (float)__ldcg(L.x + p);
+    case B_SCATTER:
+      for (int u = tid; u < g.per; u += 256) {
+        const long long p = q0 + u;
+        if (p < L.np) cur[L.cell[p]] = (float)__ldcg(L.x + p);
+      }
       break;
-    }
     case B_RESTRICT: {
       const int nc = L.n / 2;
-      const int q = tile * 256 + tid;
-      if (q < nc * nc * nc)
-        restrict_cell<float>(cur, L.s32, S.lev[g.lev + 1].s32, L.typ, L.P, q / (nc * nc), (q / nc) % nc, q % nc);
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
+        if (q < (long long)nc * nc * nc)
+          restrict_cell<float>(cur, L.s32, S.lev[g.lev + 1].s32, L.typ, L.P, (int)(q / (nc * nc)), (int)(q / nc) % nc,
+                               (int)(q % nc));
+      }
       break;
     }
     case B_PROLONG: {
       const int n = L.n;
-      const int q = tile * 256 + tid;
-      if (q < n * n * n) {
-        const BLevel& C = S.lev[g.lev + 1];
+      const BLevel& C = S.lev[g.lev + 1];
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
+        if (q >= L.N) break;
+        const int i = (int)(q / (n * n)), j = (int)(q / n) % n, k = (int)(q % n);
         if (S.prolong == 1)
-          prolong_tri_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, q / (n * n), (q / n) % n, q % n);
+          prolong_tri_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, i, j, k);
         else
-          prolong_pc_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, q / (n * n), (q / n) % n, q % n);
+          prolong_pc_cell<float>(C.e32, cur, L.typ, C.typ, n, 0, i, j, k);
       }
       break;
     }
     case B_RES_IN: {
       const int m = L.n - 4;
-      const int q = tile * 256 + tid;
-      if (q < m * m * m) resid_z32_in_cell(L.e32, S.s0, S.s, L.typ, L.P, 2 + q / (m * m), 2 + (q / m) % m, 2 + q % m);
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
+        if (q < (long long)m * m * m)
+          resid_z32_in_cell(L.e32, S.s0, S.s, L.typ, L.P, 2 + (int)(q / (m * m)), 2 + (int)(q / m) % m,
+                            2 + (int)(q % m));
+      }
       break;
     }
-    case B_RES_SHELL: {
-      const int q = tile * 256 + tid;
-      if (q < g.count) resid_z32_shell_cell(L.e32, S.s0, S.s, L.typ, L.P, q);
+    case B_RES_SHELL:
+      for (int u = tid; u < g.per; u += 256) {
+        const long long q = q0 + u;
+        if (q < g.count) resid_z32_shell_cell(L.e32, S.s0, S.s, L.typ, L.P, (int)q);
+      }
       break;
-    }
-    case B_RES2: {
-      const int r = tile * 256 + tid;
-      if (r < S.n2) resid2_row(S.e64, S.s0, S.s, S.p2_cell, S.p2_ptr, S.p2_col, S.p2_val, r);
+    case B_RES2:
+      for (int u = tid; u < g.per; u += 256) {
+        const long long r = q0 + u;
+        if (r < S.n2) resid2_row(S.e64, S.s0, S.s, S.p2_cell, S.p2_ptr, S.p2_col, S.p2_val, (int)r);
+      }
       break;
-    }
     default:
       break;
   }
 }
 
+constexpr int kWordStride = 16;  // claim words 128 bytes apart: one L2 line per solve
+
+// seg holds the solves' chains one after another (solve s: sbase[s] ..
+// sbase[s] + slen[s]).  word[s] = (current segment << 32) | tiles not yet
+// handed out; it and finished start as the host sets them (a retired solve
+// starts at the end of its chain and counts as finished).  Warp 0 of a block
+// reads the words of up to 32 solves at once, in the order `order` (largest
+// solve first) from a start that moves past each claim (so the blocks spread
+// over the solves), and claims a tile from the first with tiles left
+// (compare-and-swap on the count).
 __global__ void __launch_bounds__(256, 2)
-    k_batch_cycle(const BSolve* __restrict__ sol, const BSeg* __restrict__ seg, int nseg, long long nticket,
-                  unsigned long long* ticket, unsigned int* done, const int* __restrict__ active, double* norms,
-                  unsigned int* err, long long spin_limit) {
-  __shared__ long long s_t;
-  __shared__ int s_seg, s_go;
+    k_batch_cycle(const BSolve* __restrict__ sol, const BSeg* __restrict__ seg, const int* __restrict__ sbase,
+                  const int* __restrict__ slen, const int* __restrict__ order, int nb, unsigned long long* word,
+                  unsigned int* done, unsigned int* finished, double* norms, unsigned int* err,
+                  long long spin_limit) {
+  __shared__ int s_solve, s_seg, s_tile, s_state;
+  int start = blockIdx.x % nb;
+  long long idle = 0;
+  unsigned int nap = 32;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const long long t = (long long)atomicAdd(ticket, 1ull);
-      int si = -1, go = 0;
-      if (t < nticket) {
-        int lo = 0, hi = nseg - 1;  // the last segment with t0 <= t
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (seg[mid].t0 <= t)
-            lo = mid;
-          else
-            hi = mid - 1;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      // 0: no work yet, 1: a tile, 2: leave.  Plain polls: an acquire would
+      // invalidate this SM's L1 under the other resident block's stencil reads;
+      // the acquiring fence follows a claim.
+      int state = 0;
+      if (lane == 0 &&
+          (*(volatile unsigned int*)err != 0u || *(volatile unsigned int*)finished >= (unsigned int)nb))
+        state = 2;
+      state = __shfl_sync(0xffffffffu, state, 0);
+      for (int base = 0; base < nb && state == 0; base += 32) {
+        const int k = base + lane;
+        int sv = 0;
+        unsigned long long w = 0ull;
+        if (k < nb) {
+          sv = order[(start + k) % nb];
+          w = *(volatile unsigned long long*)(word + (size_t)sv * kWordStride);
         }
-        si = lo;
-        const BSeg& g = seg[si];
-        go = active[g.solve] && *(volatile unsigned int*)err == 0u;
-        if (go && g.prev >= 0) {
-          const unsigned int need = (unsigned int)seg[g.prev].ntiles;
-          long long spins = 0;
-          while (ld_acquire(done + g.prev) < need) {
-            if (*(volatile unsigned int*)err) {
-              go = 0;
-              break;
+        unsigned int cand = __ballot_sync(0xffffffffu, k < nb && (w & 0xffffffffull) != 0ull);
+        while (cand != 0u && state == 0) {
+          const int src = __ffs(cand) - 1;
+          cand &= cand - 1u;
+          const unsigned long long wc = __shfl_sync(0xffffffffu, w, src);
+          const int svc = __shfl_sync(0xffffffffu, sv, src);
+          int got = 0;
+          if (lane == 0) got = atomicCAS(word + (size_t)svc * kWordStride, wc, wc - 1ull) == wc;
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (got) {
+            state = 1;
+            start = (start + base + src + 1) % nb;
+            if (lane == 0) {
+              const int si = sbase[svc] + (int)(wc >> 32);
+              s_solve = svc;
+              s_seg = si;
+              s_tile = seg[si].ntiles - (int)(wc & 0xffffffffull);
             }
-            if (++spins > spin_limit) {
-              atomicExch(err, 1u);
-              go = 0;
-              break;
-            }
-            __nanosleep(64);
           }
-          __threadfence();
         }
       }
-      s_t = t;
-      s_seg = si;
-      s_go = go;
+      if (state == 0) {
+        if (++idle > spin_limit) {
+          if (lane == 0) atomicExch(err, 1u);
+          state = 2;
+        } else {
+          __nanosleep(nap);
+          nap = min(nap * 2u, 1024u);
+        }
+      } else if (state == 1) {
+        idle = 0;
+        nap = 32;
+        if (lane == 0) __threadfence();  // the claimed segment's inputs, released by its predecessor's last tile
+      }
+      if (lane == 0) s_state = state;
     }
     __syncthreads();
-    const long long t = s_t;
-    const int si = s_seg, go = s_go;
+    const int state = s_state, sv = s_solve, si = s_seg, tile = s_tile;
     __syncthreads();
-    if (si < 0) break;
-    if (go) batch_tile(sol[seg[si].solve], seg[si], (int)(t - seg[si].t0), norms);
+    if (state == 2) break;
+    if (state == 0) continue;
+    batch_tile(sol[sv], sv, seg[si], tile, norms);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(done + si, 1u);
+      if (atomicAdd(done + si, 1u) + 1u == (unsigned int)seg[si].ntiles) {
+        // the segment's last tile: the solve moves on (its last segment: finished)
+        const int next = si - sbase[sv] + 1;
+        const unsigned long long nw =
+            next < slen[sv] ? ((unsigned long long)next << 32) | (unsigned int)seg[si + 1].ntiles
+                            : (unsigned long long)next << 32;
+        __threadfence();
+        atomicExch(word + (size_t)sv * kWordStride, nw);
+        if (next >= slen[sv]) atomicAdd(finished, 1u);
+      }
     }
   }
 }
@@ -2508,71 +2558,91 @@ namespace {
 
 struct BatchBuild {
   std::vector<BSeg> segs;
-  void push(int op, int lev, long long ntiles, int a = 0, int b = 0, long long first = 0, int count = 0) {
-    if (ntiles <= 0) return;
+  long long target = 76;  // tiles wanted per large segment (the other solves' segments fill the rest)
+  // a segment over count items, tiles of per items (a multiple of unit, at most
+  // maxper) chosen so that a large segment has about `target` tiles
+  void push(int op, int lev, long long count, int unit, int maxper, int a = 0, int b = 0, long long first = 0,
+            int cnt = 0) {
+    if (count <= 0) return;
+    long long per = (count + target - 1) / target;
+    per = (per + unit - 1) / unit * unit;
+    per = std::max<long long>(unit, std::min<long long>(maxper, per));
     BSeg g;
     g.op = op;
     g.lev = lev;
-    g.ntiles = (int)ntiles;
+    g.per = (int)per;
+    g.ntiles = (int)((count + per - 1) / per);
     g.a = a;
     g.b = b;
     g.first = first;
-    g.count = count;
+    g.count = cnt;
     segs.push_back(g);
   }
   // lu_solve_ws<float, double>: right-hand side, sweeps by height, scatter
   void lu(const DevLU& D, int lev, int a) {
     if (D.np == 0) return;
-    push(B_LURHS, lev, (D.np + 255) / 256, a);
+    push(B_LURHS, lev, D.np, 256, 1024, a);
     for (int h = 0; h <= D.height; ++h) {
       const long long f0 = D.toff[0][h], c = D.toff[0][h + 1] - f0;
-      push(B_SWEEPF, lev, (c + 7) / 8, 0, 0, f0, (int)c);
+      push(B_SWEEPF, lev, c, 8, 32, 0, 0, f0, (int)c);
     }
     for (int h = D.height; h >= 0; --h) {
       const long long f0 = D.toff[1][h], c = D.toff[1][h + 1] - f0;
-      push(B_SWEEPB, lev, (c + 7) / 8, 0, 0, f0, (int)c);
+      push(B_SWEEPB, lev, c, 8, 32, 0, 0, f0, (int)c);
     }
-    push(B_SCATTER, lev, (D.np + 255) / 256, a);
+    push(B_SCATTER, lev, D.np, 256, 4096, a);
+  }
+  // SMO-1 on level m: tiles of (2 jbx) x jby x per planes
+  void jacobi(const DevLevel& L, int m, int a, int b) {
+    const int jbx = (int)L.jblock.x, jby = 256 / jbx;
+    const long long gxy = (long long)((L.n + 2 * jbx - 1) / (2 * jbx)) * ((L.n + jby - 1) / jby);
+    const long long per = std::max(1ll, std::min(16ll, (gxy * L.n + target - 1) / target));
+    BSeg g;
+    g.op = B_JAC;
+    g.lev = m;
+    g.per = (int)per;
+    g.ntiles = (int)(gxy * ((L.n + per - 1) / per));
+    g.a = a;
+    g.b = b;
+    segs.push_back(g);
   }
   // vcycle_rec<float> on level m (e32 of level 0 is cleared by B_TOFLOAT)
   void vcycle(const cc_solver* S, int m) {
     const DevLevel& L = S->lev[m];
     const int M = (int)S->lev.size() - 1;
-    if (m > 0) push(B_ZERO, m, (L.N + kBatchElems - 1) / kBatchElems);
+    if (m > 0) push(B_ZERO, m, L.N, 256, 8192);
     if (m == M) {
       lu(L.lu, m, 0);
       return;
     }
-    const int jbx = (int)L.jblock.x, jby = 256 / jbx;
-    const long long jt = (long long)((L.n + 2 * jbx - 1) / (2 * jbx)) * ((L.n + jby - 1) / jby) * L.n;
     int cur = 0;
     for (int it = 0; it < S->prm.nu1; ++it) {
-      push(B_JAC, m, jt, cur, 1 - cur);
+      jacobi(L, m, cur, 1 - cur);
       cur = 1 - cur;
       lu(L.lu, m, cur);
     }
     const long long nc = L.n / 2;
-    push(B_RESTRICT, m, (nc * nc * nc + 255) / 256, cur);
+    push(B_RESTRICT, m, nc * nc * nc, 256, 4096, cur);
     vcycle(S, m + 1);
-    push(B_PROLONG, m, (L.N + 255) / 256, cur);
+    push(B_PROLONG, m, L.N, 256, 4096, cur);
     for (int it = 0; it < S->prm.nu2; ++it) {
-      push(B_JAC, m, jt, cur, 1 - cur);
+      jacobi(L, m, cur, 1 - cur);
       cur = 1 - cur;
       lu(L.lu, m, cur);
     }
-    if (cur != 0) push(B_COPY, m, (L.N + kBatchElems - 1) / kBatchElems);
+    if (cur != 0) push(B_COPY, m, L.N, 256, 8192);
   }
   // one_cycle with precision 1: the V-cycle, phi += e, the recursive residual and its norm
   void iteration(const cc_solver* S) {
     const DevLevel& L = S->lev[0];
-    push(B_TOFLOAT, 0, (L.N + kBatchElems - 1) / kBatchElems);
+    push(B_TOFLOAT, 0, L.N, 256, 8192);
     vcycle(S, 0);
-    push(B_PHIUP, 0, (L.N + kBatchElems - 1) / kBatchElems);
+    push(B_PHIUP, 0, L.N, 256, 8192);
     const long long m = L.n - 4, shell = L.N - m * m * m;
-    push(B_RES_IN, 0, (m * m * m + 255) / 256);
-    push(B_RES_SHELL, 0, (shell + 255) / 256, 0, 0, 0, (int)shell);
-    push(B_RES2, 0, (L.n2 + 255) / 256);
-    push(B_NORM, 0, (L.N + kBatchElems - 1) / kBatchElems);
+    push(B_RES_IN, 0, m * m * m, 256, 4096);
+    push(B_RES_SHELL, 0, shell, 256, 4096, 0, 0, 0, (int)shell);
+    push(B_RES2, 0, L.n2, 256, 1024);
+    push(B_NORM, 0, L.N, 256, 8192);
   }
 };
 
@@ -3214,29 +3284,20 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
     CK(cudaStreamSynchronize(s[i]->stream));
     rel[i] = rn[i] > 0 ? std::sqrt(*s[i]->hnorm) / rn[i] : 0.0;
   }
-  // the segments of one iteration of every solve, interleaved step by step
-  std::vector<std::vector<BSeg>> prog(nb);
-  size_t longest = 0;
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle, 256, 0));
+  const int grid = std::max(1, per_sm) * S->nsm;
+  // the segments of one iteration of every solve, solve after solve
+  std::vector<BSeg> segs;
+  std::vector<int> sbase(nb), slen(nb);
   for (int i = 0; i < nb; ++i) {
     BatchBuild bb;
+    bb.target = std::max(16, grid / 4);
     bb.iteration(s[i]);
-    prog[i] = std::move(bb.segs);
-    longest = std::max(longest, prog[i].size());
+    sbase[i] = (int)segs.size();
+    slen[i] = (int)bb.segs.size();
+    segs.insert(segs.end(), bb.segs.begin(), bb.segs.end());
   }
-  std::vector<BSeg> segs;
-  std::vector<int> last(nb, -1);
-  long long nticket = 0;
-  for (size_t k = 0; k < longest; ++k)
-    for (int i = 0; i < nb; ++i) {
-      if (k >= prog[i].size()) continue;
-      BSeg g = prog[i][k];
-      g.solve = i;
-      g.prev = last[i];
-      g.t0 = nticket;
-      nticket += g.ntiles;
-      last[i] = (int)segs.size();
-      segs.push_back(g);
-    }
   std::vector<BSolve> bs(nb);
   for (int i = 0; i < nb; ++i) {
     const cc_solver* Si = s[i];
@@ -3259,12 +3320,14 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
   struct Bufs {
     BSolve* sol = nullptr;
     BSeg* seg = nullptr;
+    int *sbase = nullptr, *slen = nullptr, *order = nullptr;
     unsigned int* done = nullptr;
-    unsigned long long* ticket = nullptr;
-    int* active = nullptr;
+    unsigned long long* word = nullptr;
+    unsigned int* finished = nullptr;
     double* norms = nullptr;
     unsigned int* err = nullptr;
-    int* hactive = nullptr;
+    unsigned long long* hword = nullptr;  // pinned: claim words and the finished count of the next launch
+    unsigned int* hfinished = nullptr;
     double* hnorms = nullptr;
     unsigned int* herr = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -3272,12 +3335,16 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
       if (exec) cudaGraphExecDestroy(exec);
       cudaFree(sol);
       cudaFree(seg);
+      cudaFree(sbase);
+      cudaFree(slen);
+      cudaFree(order);
       cudaFree(done);
-      cudaFree(ticket);
-      cudaFree(active);
+      cudaFree(word);
+      cudaFree(finished);
       cudaFree(norms);
       cudaFree(err);
-      if (hactive) cudaFreeHost(hactive);
+      if (hword) cudaFreeHost(hword);
+      if (hfinished) cudaFreeHost(hfinished);
       if (hnorms) cudaFreeHost(hnorms);
       if (herr) cudaFreeHost(herr);
     }
@@ -3285,20 +3352,30 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
   const int nseg = (int)segs.size();
   CK(cudaMalloc((void**)&B.sol, sizeof(BSolve) * nb));
   CK(cudaMalloc((void**)&B.seg, sizeof(BSeg) * std::max(1, nseg)));
+  CK(cudaMalloc((void**)&B.sbase, sizeof(int) * nb));
+  CK(cudaMalloc((void**)&B.slen, sizeof(int) * nb));
+  CK(cudaMalloc((void**)&B.order, sizeof(int) * nb));
   CK(cudaMalloc((void**)&B.done, sizeof(unsigned int) * std::max(1, nseg)));
-  CK(cudaMalloc((void**)&B.ticket, sizeof(unsigned long long)));
-  CK(cudaMalloc((void**)&B.active, sizeof(int) * nb));
+  CK(cudaMalloc((void**)&B.word, sizeof(unsigned long long) * kWordStride * nb));
+  CK(cudaMalloc((void**)&B.finished, sizeof(unsigned int)));
   CK(cudaMalloc((void**)&B.norms, sizeof(double) * nb));
   CK(cudaMalloc((void**)&B.err, sizeof(unsigned int)));
-  CK(cudaMallocHost((void**)&B.hactive, sizeof(int) * nb));
+  CK(cudaMallocHost((void**)&B.hword, sizeof(unsigned long long) * kWordStride * nb));
+  std::memset(B.hword, 0, sizeof(unsigned long long) * kWordStride * nb);
+  CK(cudaMallocHost((void**)&B.hfinished, sizeof(unsigned int)));
   CK(cudaMallocHost((void**)&B.hnorms, sizeof(double) * nb));
   CK(cudaMallocHost((void**)&B.herr, sizeof(unsigned int)));
   CK(cudaMemcpy(B.sol, bs.data(), sizeof(BSolve) * nb, cudaMemcpyHostToDevice));
   if (nseg) CK(cudaMemcpy(B.seg, segs.data(), sizeof(BSeg) * nseg, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.sbase, sbase.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.slen, slen.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  {  // largest solves first
+    std::vector<int> order(nb);
+    for (int i = 0; i < nb; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return s[x]->lev[0].N > s[y]->lev[0].N; });
+    CK(cudaMemcpy(B.order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  }
   CK(cudaMemset(B.err, 0, sizeof(unsigned int)));
-  int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle, 256, 0));
-  const int grid = std::max(1, per_sm) * S->nsm;
   const long long spins = S->prm.lu_barrier_spins > 0 ? (long long)S->prm.lu_barrier_spins : kBarrierSpins;
   // one iteration of every live solve: the active flags in, the counters cleared,
   // the persistent launch, the residual norms and the error flag out
@@ -3306,12 +3383,12 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
   {
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
-    cudaMemcpyAsync(B.active, B.hactive, sizeof(int) * nb, cudaMemcpyHostToDevice, q);
-    cudaMemsetAsync(B.ticket, 0, sizeof(unsigned long long), q);
+    cudaMemcpyAsync(B.word, B.hword, sizeof(unsigned long long) * kWordStride * nb, cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(B.finished, B.hfinished, sizeof(unsigned int), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(B.done, 0, sizeof(unsigned int) * std::max(1, nseg), q);
     cudaMemsetAsync(B.norms, 0, sizeof(double) * nb, q);
-    k_batch_cycle<<<grid, 256, 0, q>>>(B.sol, B.seg, nseg, nticket, B.ticket, B.done, B.active, B.norms, B.err,
-                                       spins);
+    k_batch_cycle<<<grid, 256, 0, q>>>(B.sol, B.seg, B.sbase, B.slen, B.order, nb, B.word, B.done, B.finished,
+                                       B.norms, B.err, spins);
     cudaMemcpyAsync(B.hnorms, B.norms, sizeof(double) * nb, cudaMemcpyDeviceToHost, q);
     cudaMemcpyAsync(B.herr, B.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, q);
     CK(cudaStreamEndCapture(q, &g));
@@ -3350,7 +3427,13 @@ cc_status cc_solve_batch_persistent(cc_solver* const* s, int nb, const double* c
       ++nlive;
     }
     if (nlive == 0) break;
-    for (int i = 0; i < nb; ++i) B.hactive[i] = live[i];
+    // live solves start their chains; retired ones start at the end (finished)
+    *B.hfinished = 0;
+    for (int i = 0; i < nb; ++i) {
+      B.hword[(size_t)i * kWordStride] =
+          live[i] ? (unsigned long long)segs[sbase[i]].ntiles : (unsigned long long)slen[i] << 32;
+      if (!live[i]) ++*B.hfinished;
+    }
     CK(cudaGraphLaunch(B.exec, q));
     CK(cudaStreamSynchronize(q));
     if (*B.herr) {

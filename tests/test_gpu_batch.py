@@ -155,10 +155,11 @@ def test_persistent_batch_rejects_other_precisions(pbatch):
 
 
 def test_persistent_batch_wait_timeout(pbatch):
-    """Segment waits bounded at one poll give up while the previous segment is
-    still running: the launch skips the rest and ends, the call reports
-    CC_ERR_TIMEOUT, and the context stays usable (a normal batch follows).  No
-    wait is left open: every block returns once the flag is raised."""
+    """Idle polls bounded at one: a block that finds every tile of the solve's
+    current segment handed out gives up, the launch ends early, the call
+    reports CC_ERR_TIMEOUT, and the context stays usable (a normal batch
+    follows).  No wait is left open: every block returns once the flag is
+    raised."""
     from paper_2410_05865_gb300 import ccmg
     p = W.sphere_problem(64, radius=0.2)
     S = ccmg.Solver(p.n, p.shapes, p.shape_bc, p.box_bc, device=0, precision=1, lu_barrier_spins=1)

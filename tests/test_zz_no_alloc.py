@@ -99,13 +99,13 @@ def test_static_fp32_factors_twice():
 
 
 def test_static_rejects_too_many_rows():
-    """A sphere of radius 0.45 at 192^3 has about 2.8e5 phi2 rows on its finest
+    """A sphere of radius 0.40 at 224^3 has about 3.05e5 phi2 rows on its finest
     level, more than the 262144 the static array holds."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2410_05865_gb300 import ccmg
-    n = 192
-    prob = W.sphere_problem(n, radius=0.45)
+    n = 224
+    prob = W.sphere_problem(n, radius=0.40)
     S = ccmg.Solver(n, prob.shapes, prob.shape_bc, prob.box_bc, device=0)
     try:
         assert S.info.n_phi2[0] > 262144

@@ -480,6 +480,10 @@ def run_ours(args):
                        "levels": [info.n[m] for m in range(info.n_levels)],
                        "phi2_per_level_seed0": [info.n_phi2[m] for m in range(info.n_levels)],
                        "lu_entries_per_level_seed0": [info.lu_entries[m] for m in range(info.n_levels)],
+                       "smo1_kernel_per_level_seed0": [
+                           f"march 32x{info.jacobi_march[m]}" if info.jacobi_march[m] else
+                           f"direct {info.jacobi_block[m][0]}x{info.jacobi_block[m][1]}"
+                           for m in range(info.n_levels - 1)],
                        "v_cycles": iters, "factor_mean_per_seed": [h[1] for h in head_stats],
                        "factor_asymptotic_per_seed": [h[2] for h in head_stats], "omega": 0.5, "nu1": 3, "nu2": 3,
                        "precision": ["fp64",

@@ -132,6 +132,9 @@ typedef struct {
                         persistent batch (cc_solve_batch_persistent, first solver's
                         value); past it the launch stops and the call returns
                         CC_ERR_TIMEOUT.  0: 2^24 polls, about a second (0) */
+  int smo1_kernel;    /* SMO-1 kernels the set-up autotuner may pick: 0 the direct kernel's
+                        tile shapes and the plane-marching kernel; 1 the direct kernel
+                        only; 2 the plane-marching kernel only (0) */
 } cc_params;
 
 typedef struct {
@@ -158,6 +161,10 @@ typedef struct {
   double ms_setup_device;
   int jacobi_block[16][2];    /* SMO-1 tile chosen by the set-up autotuner per level:
                                  threads along k (two cells each) x rows along j */
+  int jacobi_march[16];       /* 0: that tile of the direct SMO-1 kernel; 8 or 16: the
+                                 plane-marching kernel (32 x 8 or 32 x 16 threads over
+                                 (k, j), 16 planes along i per block, the current plane
+                                 staged in shared memory) won the autotuner */
 } cc_info;
 
 /* Fills the defaults given above. */

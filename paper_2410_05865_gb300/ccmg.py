@@ -47,7 +47,7 @@ class cc_params(C.Structure):
                 ("krylov", C.c_int), ("krylov_restart", C.c_int), ("precision", C.c_int),
                 ("lu_schedule", C.c_int), ("krylov_cgs", C.c_int), ("prolong", C.c_int),
                 ("restriction", C.c_int), ("krylov_flexible", C.c_int), ("fmg", C.c_int),
-                ("lu_barrier_spins", C.c_int)]
+                ("lu_barrier_spins", C.c_int), ("smo1_kernel", C.c_int)]
 
 
 class cc_stats(C.Structure):
@@ -61,7 +61,7 @@ class cc_info(C.Structure):
                 ("phi2_nnz", C.c_longlong * 16), ("n_cut", C.c_int), ("n_patches", C.c_int),
                 ("cut_nodes", C.c_longlong), ("patch_nodes", C.c_longlong),
                 ("ms_setup_host", C.c_double), ("ms_setup_device", C.c_double),
-                ("jacobi_block", (C.c_int * 2) * 16)]
+                ("jacobi_block", (C.c_int * 2) * 16), ("jacobi_march", C.c_int * 16)]
 
 
 # Every symbol include/ccmg.h declares, with its ctypes signature.

@@ -206,6 +206,72 @@ __global__ void __launch_bounds__(256) k_jacobi(const T* __restrict__ phi_in, co
                  2 * (blockIdx.x * blockDim.x + threadIdx.x));
 }
 
+// SMO-1 marching along i with the current plane staged in shared memory: a
+// block owns a TK x TJ tile of (k, j) and kMarchPlanes consecutive planes;
+// each thread keeps phi at (i-2 .. i+2, j, k) in registers and loads one new
+// value per plane, and the plane i (with a two-cell halo in j and k) is
+// written to shared memory once for the j and k neighbours.  So each value
+// comes from HBM about once (the halo from L2), instead of the 13 cached
+// reads of the direct kernel.  The interior rows use interior13 on the same
+// operands in the same order as k_jacobi (the same sums, up to where the
+// compiler fuses a product into an FMA); rows next to the box take
+// apply_regular.
+constexpr int kMarchPlanes = 16;
+
+template <class T, int TK, int TJ>
+__global__ void __launch_bounds__(TK * TJ)
+    k_jacobi_march(const T* __restrict__ phi_in, const T* __restrict__ s, T* __restrict__ phi_out,
+                   const uint8_t* __restrict__ typ, StencilP P) {
+  __shared__ T pl[TJ + 4][TK + 4];
+  const int n = P.n, nn = n * n;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ;
+  const int k = k0 + tx, j = j0 + ty;
+  const int i0 = blockIdx.z * kMarchPlanes, i1 = min(n, i0 + kMarchPlanes);
+  const bool in = k < n && j < n;
+  auto at = [&](int i, int jj, int kk) -> T {
+    return (i >= 0 && i < n && jj >= 0 && jj < n && kk >= 0 && kk < n) ? phi_in[(i * n + jj) * n + kk] : T(0);
+  };
+  T q0 = at(i0 - 2, j, k), q1 = at(i0 - 1, j, k), q2 = at(i0, j, k), q3 = at(i0 + 1, j, k);
+  const T inv = st_inv<T>(P);
+  const T w = st_winv<T>(P, 2, 2, 2);
+  const int cj = pos_class(j, n), ck = pos_class(k, n);
+  for (int i = i0; i < i1; ++i) {
+    const T q4 = at(i + 2, j, k);
+    __syncthreads();  // the previous plane's readers are done
+    pl[ty + 2][tx + 2] = q2;
+    if (tx < 2) {
+      pl[ty + 2][tx] = at(i, j, k0 - 2 + tx);
+      pl[ty + 2][TK + 2 + tx] = at(i, j, k0 + TK + tx);
+    }
+    if (ty < 2) {
+      pl[ty][tx + 2] = at(i, j0 - 2 + ty, k);
+      pl[TJ + 2 + ty][tx + 2] = at(i, j0 + TJ + ty, k);
+    }
+    __syncthreads();
+    if (in) {
+      const int idx = (i * n + j) * n + k;
+      T res = q2;
+      if (typ[idx] == 1) {
+        const int ci = pos_class(i, n);
+        if (ci == 2 && cj == 2 && ck == 2) {
+          const T l = interior13<T>(q2, q3, q1, pl[ty + 3][tx + 2], pl[ty + 1][tx + 2], pl[ty + 2][tx + 3],
+                                    pl[ty + 2][tx + 1], q4, q0, pl[ty + 4][tx + 2], pl[ty][tx + 2],
+                                    pl[ty + 2][tx + 4], pl[ty + 2][tx], inv);
+          res = fma_t(w, s[idx] - l, q2);
+        } else {
+          res = fma_t(st_winv<T>(P, ci, cj, ck), s[idx] - apply_regular<T>(phi_in, i, j, k, P), q2);
+        }
+      }
+      phi_out[idx] = res;
+    }
+    q0 = q1;
+    q1 = q2;
+    q2 = q3;
+    q3 = q4;
+  }
+}
+
 // The interior row, exactly, for values held in FP32.  An FP32 value is
 // m 2^(e-150) with an integer m < 2^24 (e = 1 and no implicit bit for a
 // subnormal).  In units of 2^(emax-180), emax the largest e among the row's 13
@@ -1099,6 +1165,7 @@ struct DevLevel {
   float *s32 = nullptr, *e32 = nullptr, *tmp32 = nullptr;  // mixed precision V-cycle
   double *fr = nullptr, *fphi = nullptr;  // Alg. FMG: this level's data and solution (levels >= 1)
   dim3 jblock = dim3(16, 8);  // SMO-1 tile (pairs along k x rows along j), tuned at set-up
+  int jmarch = 0;             // 0: k_jacobi with jblock; 8 or 16: k_jacobi_march with 32 x jmarch tiles
   template <class T> T* bs();
   template <class T> T* be();
   template <class T> T* btmp();
@@ -1927,18 +1994,33 @@ void lu_solve(cc_solver* S, DevLU& D, const T* s, T* phi) {
 }
 
 template <class T>
-void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
-  const int block = 256;
-  ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
-  (void)block;
-  const dim3 tb = L.jblock;
+void launch_jacobi(cc_solver* S, const DevLevel& L, int march, dim3 tb, const T* in, const T* s, T* out) {
+  if (march) {
+    const dim3 grid((L.n + 31) / 32, (L.n + march - 1) / march, (L.n + kMarchPlanes - 1) / kMarchPlanes);
+    if (march == 8)
+      k_jacobi_march<T, 32, 8><<<grid, dim3(32, 8), 0, S->stream>>>(in, s, out, L.typ, L.P);
+    else
+      k_jacobi_march<T, 32, 16><<<grid, dim3(32, 16), 0, S->stream>>>(in, s, out, L.typ, L.P);
+    return;
+  }
   const dim3 grid((L.n + 2 * tb.x - 1) / (2 * tb.x), (L.n + tb.y - 1) / tb.y, L.n);
   k_jacobi<T><<<grid, tb, 0, S->stream>>>(in, s, out, L.typ, L.P);
 }
 
-// Set-up autotuner of the SMO-1 tile: times each candidate shape on the
-// level's own work arrays (contents irrelevant, results discarded) and keeps
-// the fastest for the V-cycle's precision.
+template <class T>
+void jacobi(cc_solver* S, DevLevel& L, const T* in, const T* s, T* out) {
+  ProfScope ps(S, P_JACOBI, (3.0 * sizeof(T) + 1.0) * L.N);
+  launch_jacobi<T>(S, L, L.jmarch, L.jblock, in, s, out);
+}
+
+// The direct kernel's tile to keep beside a marching pick (the persistent batch
+// runs the direct kernel's pairs): 16 x 16.
+dim3 march_free_tile(dim3 tb, int march) { return march ? dim3(16, 16) : tb; }
+
+// Set-up autotuner of SMO-1: times each candidate (the direct kernel's tile
+// shapes and the plane-marching kernel's two tiles, as params.smo1_kernel
+// allows) on the level's own work arrays (contents irrelevant, results
+// discarded) and keeps the fastest for the V-cycle's precision.
 template <class T>
 cc_status tune_jacobi(cc_solver* S, DevLevel& L, T* a, T* b, T* c) {
   static const int cand[][2] = {{16, 8}, {32, 4}, {8, 16}, {16, 16}, {32, 8}, {64, 2},
@@ -1950,13 +2032,18 @@ cc_status tune_jacobi(cc_solver* S, DevLevel& L, T* a, T* b, T* c) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   dim3 pick(16, 8);
-  for (const auto& cb : cand) {
-    const dim3 tb(cb[0], cb[1]);
-    if (2 * (int)tb.x > 2 * L.n) continue;
-    const dim3 grid((L.n + 2 * tb.x - 1) / (2 * tb.x), (L.n + tb.y - 1) / tb.y, L.n);
-    for (int w = 0; w < 2; ++w) k_jacobi<T><<<grid, tb, 0, S->stream>>>(a, b, c, L.typ, L.P);
+  int pick_march = 0;
+  // the direct kernel's tile shapes, then the plane-marching kernel (32 x 8, 32 x 16)
+  const int mode = S->prm.smo1_kernel;
+  const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+  for (int q = 0; q < ncand + 2; ++q) {
+    const int march = q < ncand ? 0 : (q == ncand ? 8 : 16);
+    if ((mode == 1 && march) || (mode == 2 && !march)) continue;
+    const dim3 tb = q < ncand ? dim3(cand[q][0], cand[q][1]) : dim3(32, march);
+    if (!march && 2 * (int)tb.x > 2 * L.n) continue;
+    for (int w = 0; w < 2; ++w) launch_jacobi<T>(S, L, march, tb, a, b, c);
     CK(cudaEventRecord(e0, S->stream));
-    for (int r = 0; r < 5; ++r) k_jacobi<T><<<grid, tb, 0, S->stream>>>(a, b, c, L.typ, L.P);
+    for (int r = 0; r < 5; ++r) launch_jacobi<T>(S, L, march, tb, a, b, c);
     CK(cudaEventRecord(e1, S->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -1964,11 +2051,13 @@ cc_status tune_jacobi(cc_solver* S, DevLevel& L, T* a, T* b, T* c) {
     if (ms < best) {
       best = ms;
       pick = tb;
+      pick_march = march;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  L.jblock = pick;
+  L.jblock = march_free_tile(pick, pick_march);
+  L.jmarch = pick_march;
   return CC_OK;
 }
 
@@ -2713,6 +2802,7 @@ void cc_default_params(cc_params* p) {
   p->krylov_flexible = 1;
   p->fmg = 0;
   p->lu_barrier_spins = 0;
+  p->smo1_kernel = 0;
 }
 
 const char* cc_status_str(cc_status st) {
@@ -2764,7 +2854,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
   if (S->prm.nu1 < 0 || S->prm.nu2 < 0 || !(S->prm.omega > 0) || S->prm.max_iter < 0 || S->prm.lu_leaf < 1 ||
       S->prm.precision < 0 || S->prm.precision > 3 || S->prm.lu_schedule < 0 || S->prm.lu_schedule > 2 ||
       S->prm.prolong < 0 || S->prm.prolong > 1 || S->prm.restriction < 0 || S->prm.restriction > 1 ||
-      S->prm.fmg < 0 || S->prm.lu_barrier_spins < 0) {
+      S->prm.fmg < 0 || S->prm.lu_barrier_spins < 0 || S->prm.smo1_kernel < 0 || S->prm.smo1_kernel > 2) {
     delete S;
     return CC_ERR_INVALID_ARG;
   }
@@ -3004,6 +3094,7 @@ cc_status cc_setup(const cc_geometry* g, const cc_params* p, int device, cc_solv
       TRY(tune_jacobi<double>(S, D, D.e, D.s, D.tmp));
     S->info.jacobi_block[m][0] = (int)D.jblock.x;
     S->info.jacobi_block[m][1] = (int)D.jblock.y;
+    S->info.jacobi_march[m] = D.jmarch;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     st = CC_ERR_CUDA;

@@ -161,3 +161,52 @@ def test_diverging_iteration_reported(case):
         rc = e.status
     K.close()
     assert rc == 7, rc
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_smo1_kernels_agree(case, kernel, precision):
+    """The direct SMO-1 kernel (1) and the plane-marching kernel with its
+    shared-memory plane (2) compute the same rows (up to rounding): the solves
+    take the same V-cycles with the same residual history as the autotuner's
+    pick, in FP64 and in the FP32 V-cycle."""
+    st0, rc0, err0 = run(case, precision=precision)
+    st, rc, err = run(case, smo1_kernel=kernel, precision=precision)
+    assert rc == 0 and st.iters == st0.iters
+    h0 = np.array(st0.resid_hist[:st0.iters])
+    h = np.array(st.resid_hist[:st.iters])
+    assert np.allclose(h, h0, rtol=1e-6, atol=0)
+    assert err < 1e-7
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_smo1_march_matches_direct_64(precision):
+    """One SMO-1 sweep at 64^3 (three ellipsoids, two-plus marching blocks
+    along every axis, a ragged last block of planes at the coarser levels):
+    the marching kernel's output equals the direct kernel's to FP64 rounding
+    (the same row sums; the compiler may fuse a product into an FMA in one
+    kernel and not the other), through cc_jacobi, for solvers set up for
+    either precision."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_05865_gb300 import ccmg
+    prob = W.ellipsoids_problem(64, 0)
+    A = ccmg.Solver(64, prob.shapes, prob.shape_bc, prob.box_bc, device=0, smo1_kernel=1, precision=precision)
+    B = ccmg.Solver(64, prob.shapes, prob.shape_bc, prob.box_bc, device=0, smo1_kernel=2, precision=precision)
+    try:
+        assert all(B.info.jacobi_march[m] in (8, 16) for m in range(B.info.n_levels - 1))
+        assert all(A.info.jacobi_march[m] == 0 for m in range(A.info.n_levels - 1))
+        rng = np.random.default_rng(5)
+        for m in range(A.info.n_levels - 1):
+            n = A.info.n[m]
+            phi = torch.from_numpy(rng.standard_normal(n ** 3)).cuda()
+            rhs = torch.from_numpy(rng.standard_normal(n ** 3)).cuda()
+            oa = torch.zeros_like(phi)
+            ob = torch.zeros_like(phi)
+            A.jacobi(m, phi, rhs, oa)
+            B.jacobi(m, phi, rhs, ob)
+            torch.cuda.synchronize()
+            assert (oa - ob).abs().max().item() <= 1e-13 * oa.abs().max().item(), m
+    finally:
+        A.close()
+        B.close()

@@ -70,6 +70,7 @@ def parse():
                     help="0 the paper's 2^-3 sum over the children; 1 full weighting")
     ap.add_argument("--cgs", type=int, default=1,
                     help="GMRES orthogonalisation: 0 modified, 1 classical Gram-Schmidt (two fused passes)")
+    ap.add_argument("--lu-leaf", type=int, default=128, help="nested-dissection leaf size of the LU factors")
     ap.add_argument("--lu-schedule", type=int, default=0,
                     help="LU sweeps: 0 per-height programmatic launches, 1 one cooperative launch, 2 plain launches")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 reference, variants and order runs")
@@ -341,7 +342,7 @@ def run_ours(args):
     seeds = seeds_of(args)
     kw = dict(precision=args.precision, krylov=args.krylov, min_coarse_n=args.min_n, krylov_restart=args.restart,
               max_iter=2000, prolong=args.prolong, restriction=args.restriction, krylov_cgs=args.cgs,
-              lu_schedule=args.lu_schedule)
+              lu_schedule=args.lu_schedule, lu_leaf=args.lu_leaf)
     stream = torch.cuda.Stream()
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     probs, solvers, inputs, host_inputs, phis, setup_s = [], [], [], [], [], []

@@ -1370,12 +1370,12 @@ constexpr int kWordStride = 16;  // claim words 128 bytes apart: one L2 line per
 // solve first) from a start that moves past each claim (so the blocks spread
 // over the solves), and claims a tile from the first with tiles left
 // (compare-and-swap on the count).
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_batch_cycle(const BSolve* __restrict__ sol, const BSeg* __restrict__ seg, const int* __restrict__ sbase,
                   const int* __restrict__ slen, const int* __restrict__ order, int nb, unsigned long long* word,
                   unsigned int* done, unsigned int* finished, double* norms, unsigned int* err,
                   long long spin_limit) {
-  __shared__ int s_solve, s_seg, s_tile, s_state;
+  __shared__ int s_solve, s_seg, s_tile, s_take, s_state;
   int start = blockIdx.x % nb;
   long long idle = 0;
   unsigned int nap = 32;
@@ -1404,8 +1404,11 @@ __global__ void __launch_bounds__(256, 2)
           cand &= cand - 1u;
           const unsigned long long wc = __shfl_sync(0xffffffffu, w, src);
           const int svc = __shfl_sync(0xffffffffu, sv, src);
+          // several tiles at once while many are left (fewer claims), one near the end
+          const unsigned int left = (unsigned int)(wc & 0xffffffffull);
+          const unsigned int take = left >= 256u ? 4u : (left >= 64u ? 2u : 1u);
           int got = 0;
-          if (lane == 0) got = atomicCAS(word + (size_t)svc * kWordStride, wc, wc - 1ull) == wc;
+          if (lane == 0) got = atomicCAS(word + (size_t)svc * kWordStride, wc, wc - take) == wc;
           got = __shfl_sync(0xffffffffu, got, 0);
           if (got) {
             state = 1;
@@ -1414,7 +1417,8 @@ __global__ void __launch_bounds__(256, 2)
               const int si = sbase[svc] + (int)(wc >> 32);
               s_solve = svc;
               s_seg = si;
-              s_tile = seg[si].ntiles - (int)(wc & 0xffffffffull);
+              s_tile = seg[si].ntiles - (int)left;
+              s_take = (int)take;
             }
           }
         }
@@ -1435,15 +1439,15 @@ __global__ void __launch_bounds__(256, 2)
       if (lane == 0) s_state = state;
     }
     __syncthreads();
-    const int state = s_state, sv = s_solve, si = s_seg, tile = s_tile;
+    const int state = s_state, sv = s_solve, si = s_seg, tile = s_tile, take = s_take;
     __syncthreads();
     if (state == 2) break;
     if (state == 0) continue;
-    batch_tile(sol[sv], sv, seg[si], tile, norms);
+    for (int u = 0; u < take; ++u) batch_tile(sol[sv], sv, seg[si], tile + u, norms);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      if (atomicAdd(done + si, 1u) + 1u == (unsigned int)seg[si].ntiles) {
+      if (atomicAdd(done + si, (unsigned int)take) + (unsigned int)take == (unsigned int)seg[si].ntiles) {
         // the segment's last tile: the solve moves on (its last segment: finished)
         const int next = si - sbase[sv] + 1;
         const unsigned long long nw =

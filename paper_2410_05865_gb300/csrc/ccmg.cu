@@ -1777,24 +1777,39 @@ cc_status upload_lu(cc_solver* S, DevLU& D, const SuperLU& F, const std::vector<
     S->err = "LU structure too large for 32-bit task indices";
     return CC_ERR_INVALID_ARG;
   }
-  // warp tasks of the per-height launches: tiles of at most 32 rows x kSegCols
-  // columns of the column-major blocks
+  // warp tasks of the per-height launches: tiles of at most 32 rows x seg
+  // columns of the column-major blocks.  seg is kSegCols where a height has
+  // tiles enough to fill the GPU several times; a height with fewer takes 16
+  // or 8 columns, more and shorter tasks, so that its launch is not as long
+  // as one warp's chain of dependent loads over 32 columns.
   std::vector<std::vector<Task>> byh[2];
   for (int sw = 0; sw < 2; ++sw) byh[sw].assign(F.height + 1, {});
-  auto tiles = [&](std::vector<Task>& out, long long off, int rows, int cols, int soff0, int out0, int src) {
+  std::vector<long long> full[2];
+  for (int sw = 0; sw < 2; ++sw) full[sw].assign(F.height + 1, 0);
+  auto ntiles = [](long long rows, long long cols) { return ((rows + 31) / 32) * ((cols + kSegCols - 1) / kSegCols); };
+  for (int s = 0; s < F.nsuper; ++s) {
+    const int k = F.sn_first[s + 1] - F.sn_first[s];
+    const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
+    full[0][F.sn_height[s]] += m > 0 ? ntiles(m, k) : 0;
+    full[1][F.sn_height[s]] += ntiles(k, k) + (m > 0 ? ntiles(k, m) : 0);
+  }
+  const long long warps = 8ll * 3 * S->nsm;  // resident warps of a sweep launch
+  auto seg_of = [&](int sw, int h) { return full[sw][h] >= 2 * warps ? kSegCols : (full[sw][h] >= warps / 2 ? 16 : 8); };
+  auto tiles = [&](std::vector<Task>& out, long long off, int rows, int cols, int soff0, int out0, int src, int seg) {
     for (int r0 = 0; r0 < rows; r0 += 32)
-      for (int c0 = 0; c0 < cols; c0 += kSegCols)
-        out.push_back({off + (long long)c0 * rows + r0, rows, std::min(32, rows - r0),
-                       std::min(kSegCols, cols - c0), soff0 + c0, out0 + r0, src});
+      for (int c0 = 0; c0 < cols; c0 += seg)
+        out.push_back({off + (long long)c0 * rows + r0, rows, std::min(32, rows - r0), std::min(seg, cols - c0),
+                       soff0 + c0, out0 + r0, src});
   };
   for (int s = 0; s < F.nsuper; ++s) {
     const int f0 = F.sn_first[s], k = F.sn_first[s + 1] - f0;
     const int m = (int)(F.sn_struct[s + 1] - F.sn_struct[s]);
     const int st0 = (int)F.sn_struct[s];
     const int hgt = F.sn_height[s];
-    if (m > 0) tiles(byh[0][hgt], F.off_w[s], m, k, f0, st0, 2);  // W (m x k): b_s contiguous, outputs b[structs]
-    tiles(byh[1][hgt], F.off_g[s], k, k, f0, f0, 0);                // G (k x k): b_s contiguous, outputs x_s
-    if (m > 0) tiles(byh[1][hgt], F.off_v[s], k, m, st0, f0, 1);  // V (k x m): x gathered through structs
+    const int sf = seg_of(0, hgt), sb = seg_of(1, hgt);
+    if (m > 0) tiles(byh[0][hgt], F.off_w[s], m, k, f0, st0, 2, sf);  // W (m x k): b_s contiguous, outputs b[structs]
+    tiles(byh[1][hgt], F.off_g[s], k, k, f0, f0, 0, sb);                // G (k x k): b_s contiguous, outputs x_s
+    if (m > 0) tiles(byh[1][hgt], F.off_v[s], k, m, st0, f0, 1, sb);  // V (k x m): x gathered through structs
   }
   std::vector<Task> all;
   for (int sw = 0; sw < 2; ++sw) {
